@@ -1,0 +1,218 @@
+/*
+ * cluster.h — C ABI of the B300 fuzzy-clustering library (libcluster.so).
+ *
+ * The library minimises f(U) = ||S - U U^T||_F^2 over row-stochastic
+ * membership matrices U (n x k, every row on the probability simplex), the
+ * model (P) of arXiv 2506.04045 Sect. 2 written with U = X^T (the paper's X is
+ * C x N with columns on the simplex; here n = N articles, k = C clusters).
+ * S is a sparse symmetric similarity matrix given in CSR form.  The solver is
+ * the paper's parallel FISTA (Algorithm 4) or plain projected gradient
+ * (Algorithm 3, momentum off), one fused GPU pass per iteration.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers marked "device" must be CUDA device (or managed) memory of the
+ *    current device; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Every call returns a cluster_status.  Nothing aborts the process; on an
+ *    error the call leaves its outputs unspecified and cluster_last_error()
+ *    returns a message for the calling thread.
+ *  - The caller owns every buffer it passes in; the library owns every
+ *    object it returns (free them with the matching destroy/free call).
+ *  - Layouts: U, U0 and U_out are n x k row-major float32 (row i = article
+ *    i's memberships, stride k).  CSR columns must be sorted and unique within
+ *    each row.
+ */
+#ifndef CLUSTER_H_
+#define CLUSTER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CLUSTER_API __attribute__((visibility("default")))
+#else
+#define CLUSTER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status codes                                                              */
+/* ------------------------------------------------------------------------ */
+typedef enum cluster_status {
+  CLUSTER_OK = 0,
+  CLUSTER_EINVAL = 1,      /* bad argument or input that fails validation      */
+  CLUSTER_ENOMEM = 2,      /* device or host allocation failed                 */
+  CLUSTER_ECUDA = 3,       /* a CUDA runtime call failed                       */
+  CLUSTER_ENONFINITE = 4,  /* NaN/Inf appeared in the iterate (report status)  */
+  CLUSTER_EMAXITER = 5,    /* report status: max_iter reached before a stop    */
+  CLUSTER_ETIMEOUT = 6,    /* a bounded wait gave up                           */
+  CLUSTER_EAGAIN = 7       /* server: the request is still pending             */
+} cluster_status;
+
+/* Arithmetic of the fused pass.  FP32: float32 iterate, products with S and
+ * Gram matrices accumulated in float32, objective/trace/norm reductions in
+ * float64.  MIXED_BF16: the copy of the iterate that the product S*U gathers
+ * and the values of S are bfloat16 (round to nearest even); a float32 master
+ * iterate is kept for the row-local update; accumulations as in FP32. */
+typedef enum cluster_precision {
+  CLUSTER_FP32 = 0,
+  CLUSTER_MIXED_BF16 = 1
+} cluster_precision;
+
+/* Step size tau.  Theorem 2.1 gives convergence of plain projected gradient
+ * for tau < 1/L with L = 4 ||S||_2 + 12 n; the experiments (Sect. 5,
+ * "Hyperparameters") replace ||S||_2 by ||S||_F.  For the two 1/L rules
+ * options.tau is a multiplier on 1/L (0 means 1). */
+typedef enum cluster_step_rule {
+  CLUSTER_STEP_CONST = 0,       /* tau = options.tau                          */
+  CLUSTER_STEP_INV_L_FROB = 1,  /* tau = options.tau / (4 ||S||_F + 12 n)     */
+  CLUSTER_STEP_INV_L_SPEC = 2   /* tau = options.tau / (4 ||S||_2 + 12 n),
+                                   ||S||_2 by power iteration on the GPU     */
+} cluster_step_rule;
+
+/* Stopping rule.  LOSS is the paper's: stop at iteration n once
+ * f(Xbar^{n-1}) - f(Xbar^n) <= tol (Algorithm 4 and the prose after it; the
+ * output is Xbar^n).  The PG rules use r_n = ||Y^n - Xbar^n||_F / tau, the
+ * gradient mapping at the extrapolated point: PG_REL stops once
+ * r_n <= tol * r_1, PG_ABS once r_n <= tol (output Xbar^n).  NONE runs
+ * max_iter iterations. */
+typedef enum cluster_stop_rule {
+  CLUSTER_STOP_LOSS = 0,
+  CLUSTER_STOP_PG_REL = 1,
+  CLUSTER_STOP_PG_ABS = 2,
+  CLUSTER_STOP_NONE = 3
+} cluster_stop_rule;
+
+/* Sparse symmetric similarity matrix S (n x n) in CSR form.
+ * row_ptr: n+1 entries, int32 (index64 = 0) or int64 (index64 = 1),
+ * row_ptr[0] = 0, row_ptr[n] = nnz; col: nnz int32 column indices, sorted
+ * and unique within each row; val: nnz float32 values.  The paper's S is the
+ * citation adjacency (s_ij = 1 if i cites or is cited by j) plus a unit
+ * diagonal (Example 4.1); weights other than 1 are accepted. */
+typedef struct cluster_csr {
+  int64_t n;
+  int64_t nnz;
+  int32_t index64;
+  int32_t _pad;
+  const void* row_ptr;
+  const int32_t* col;
+  const float* val;
+} cluster_csr;
+
+typedef struct cluster_options {
+  int32_t precision;   /* cluster_precision (default FP32)                      */
+  int32_t step_rule;   /* cluster_step_rule (default INV_L_FROB)                */
+  int32_t stop_rule;   /* cluster_stop_rule (default LOSS)                      */
+  int32_t accel;       /* 1 = FISTA (Algorithm 4), 0 = plain GPA (default 1)    */
+  int32_t borrow;      /* 1 = keep the caller's device CSR arrays (they must
+                          outlive the context); 0 = copy them (default 0)      */
+  int32_t validate;    /* 0 = none; 1 = CSR structure (sorted, in range, unit
+                          diagonal present, finite values) and U0 rows on the
+                          simplex (default); 2 = also check that S is symmetric */
+  double tau;          /* see cluster_step_rule (default 1)                     */
+  double tol;          /* stopping tolerance (default 0)                        */
+  int64_t max_iter;    /* iteration cap, >= 1 (default 1000)                    */
+  int32_t graph_chunk; /* iterations per captured CUDA graph (default 16)      */
+  int32_t _pad;
+} cluster_options;
+
+/* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */
+typedef struct cluster_report {
+  int64_t iters;       /* fused passes (gradient evaluations) executed          */
+  int64_t f_iter;      /* index n of the newest iterate whose loss is known    */
+  double f;            /* f(Xbar^{f_iter}) in float64, by the trace identity   */
+  double trace_SU;     /* sum_i <u_i, (S U)_i> of that iterate                 */
+  double gram_fro2;    /* ||U^T U||_F^2 of that iterate                        */
+  double pg_norm;      /* newest r_n = ||Y^n - Xbar^n||_F / tau                 */
+  double tau;          /* step size in use                                      */
+  double L;            /* Lipschitz bound 4 ||S|| + 12 n of the step rule       */
+  int64_t out_iter;    /* index of the iterate cluster_get_U returns            */
+  int32_t done;        /* 1 once a stop rule, max_iter or a fault ended it      */
+  int32_t status;      /* CLUSTER_OK (stopped by its rule / still running),
+                          CLUSTER_EMAXITER, or CLUSTER_ENONFINITE              */
+} cluster_report;
+
+typedef struct cluster_ctx cluster_ctx;
+
+/* Fill `opt` with the defaults listed in cluster_options. */
+CLUSTER_API void cluster_options_default(cluster_options* opt);
+
+/* Message describing the calling thread's most recent error ("" if none).
+ * The string stays valid until the thread's next library call. */
+CLUSTER_API const char* cluster_last_error(void);
+
+/* Create a solver for S (device CSR) with k clusters (1 <= k <= 128) from
+ * the start point U0 (device, n x k; every row must be on the simplex to
+ * within 1e-5).  Validates the inputs (EINVAL on failure), computes ||S||_F^2
+ * and the step size, orders the rows by degree for load balance, and
+ * evaluates the Gram matrix of U0.  The context keeps its own copy of U0.
+ * Work is enqueued on `stream`; the call returns after it completes.
+ * Sect. 3, Algorithm 4 "initialize"; Sect. 5 "Hyperparameters". */
+CLUSTER_API cluster_status cluster_init(const cluster_csr* S, int32_t k, const float* U0,
+                                        const cluster_options* opt, void* stream,
+                                        cluster_ctx** out);
+
+/* Advance by at most `iters` iterations (fewer if a stop rule fires or
+ * max_iter is reached), then fill `rep` (may be NULL).  Each iteration is one
+ * fused pass over S on the GPU (Algorithm 4's body with the second product
+ * with S replaced by linearity); the host synchronises once per call. */
+CLUSTER_API cluster_status cluster_step(cluster_ctx* ctx, int64_t iters, cluster_report* rep);
+
+/* Enqueue `iters` iterations on the context's stream and return without
+ * synchronising (no report).  For timing loops; call cluster_step(ctx, 0,
+ * &rep) afterwards to synchronise and read the state. */
+CLUSTER_API cluster_status cluster_enqueue(cluster_ctx* ctx, int64_t iters);
+
+/* Iterate until the stop rule fires or max_iter is reached, then make sure
+ * rep->f is the loss of the returned iterate (one extra objective pass if
+ * needed).  Returns CLUSTER_OK; rep->status tells how the run ended. */
+CLUSTER_API cluster_status cluster_solve(cluster_ctx* ctx, cluster_report* rep);
+
+/* Current report without doing any work. */
+CLUSTER_API cluster_status cluster_get_report(cluster_ctx* ctx, cluster_report* rep);
+
+/* Copy the output iterate (the one rep.out_iter names) into U_out (device,
+ * n x k). */
+CLUSTER_API cluster_status cluster_get_U(cluster_ctx* ctx, float* U_out);
+
+/* f(U) = ||S||_F^2 + ||U^T U||_F^2 - 2 sum_i <u_i, (S U)_i> in float64
+ * (Sect. 3, "Loss Update"), for device S and U (n x k).  Allocates and frees
+ * its own scratch; synchronises `stream`.  *f receives the value. */
+CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, const float* U,
+                                             void* stream, double* f);
+
+/* Checkpoint.  The state is everything a resumed run needs to continue bit
+ * for bit: the two newest iterates, the stored product S*Xbar^{n-1}, the
+ * float64 Gram matrices and scalars.  cluster_state_size gives the byte size;
+ * buffers are host memory. */
+CLUSTER_API cluster_status cluster_state_size(cluster_ctx* ctx, size_t* bytes);
+CLUSTER_API cluster_status cluster_get_state(cluster_ctx* ctx, void* host_buf, size_t bytes);
+CLUSTER_API cluster_status cluster_set_state(cluster_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Release everything the context owns.  NULL is ignored. */
+CLUSTER_API void cluster_destroy(cluster_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* CSR construction (host)                                                   */
+/* ------------------------------------------------------------------------ */
+/* Build the symmetric similarity matrix from an edge list (Example 4.1):
+ * s_ij = s_ji = w_e for each edge e = (src[e], dst[e]) — "i cites or is cited
+ * by j" — keeping the largest weight when a pair repeats.  w may be NULL
+ * (all weights 1).  With add_unit_diag != 0 the diagonal is 1 and self-loop
+ * edges are ignored; otherwise self-loops keep their largest weight.
+ * src/dst/w are host arrays of length m.  On success `out` receives host
+ * arrays allocated by the library (int64 row_ptr, index64 = 1, sorted
+ * columns); release them with cluster_csr_free.  EINVAL if an endpoint is
+ * outside [0, n) or a weight is not finite. */
+CLUSTER_API cluster_status cluster_csr_from_edges(int64_t n, int64_t m, const int64_t* src,
+                                                  const int64_t* dst, const float* w,
+                                                  int32_t add_unit_diag, cluster_csr* out);
+CLUSTER_API void cluster_csr_free(cluster_csr* csr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLUSTER_H_ */

@@ -28,10 +28,12 @@ from .fista import (
     OracleResult,
     csr_from_edges,
     spectral_norm,
+    momentum_factors,
+    fista_step_rows,
 )
 
 __all__ = [
     "frob2", "objective_dense", "objective_trace", "gradient_matrix", "gradient_columns",
     "hessian_apply", "duchi", "project_omega", "lipschitz", "gpa", "fista",
-    "OracleResult", "csr_from_edges", "spectral_norm",
+    "OracleResult", "csr_from_edges", "spectral_norm", "momentum_factors", "fista_step_rows",
 ]

@@ -279,6 +279,40 @@ def fista(S, U0, tau: float, tol: float = 0.0, max_iter: int = 100,
     return OracleResult(Xbar_prev, max_iter, False, losses, pgs, hist)
 
 
+def momentum_factors(n_iter: int, accel: bool = True) -> list:
+    """beta_n = (t_{n-1} - 1) / t_n for n = 1..n_iter with t_1 = 1 and
+    t_{n+1} = (1 + sqrt(1 + 4 t_n^2)) / 2 (Algorithm 4); X^n = Xbar^{n-1} +
+    beta_n (Xbar^{n-1} - Xbar^{n-2}), beta_1 = 0 since X^1 = Xbar^0."""
+    out = [0.0]
+    t = 1.0
+    for _ in range(1, n_iter):
+        t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        out.append((t - 1.0) / t_next if accel else 0.0)
+        t = t_next
+    return out
+
+
+def fista_step_rows(S, Xbar_cur, Xbar_prev, beta: float, tau: float, rows) -> np.ndarray:
+    """One iteration of Algorithm 4 evaluated only at the given articles.
+
+    X = Xbar_cur + beta (Xbar_cur - Xbar_prev) (the extrapolated point),
+    share = X^T X over all articles, then for each requested i:
+    grad_i = -4 (X s_i - share x_i) and xbar_i = Algorithm 1 applied to
+    x_i - tau grad_i.  Returns the rows of the next Xbar (float64)."""
+    S = _as_csr(S)
+    Xc = np.asarray(Xbar_cur, dtype=np.float64)
+    Xp = np.asarray(Xbar_prev, dtype=np.float64)
+    X = Xc + beta * (Xc - Xp)
+    share = X.T @ X
+    out = np.empty((len(rows), X.shape[1]))
+    for r, i in enumerate(rows):
+        lo, hi = S.indptr[i], S.indptr[i + 1]
+        Xs_i = S.data[lo:hi] @ X[S.indices[lo:hi]]
+        grad = -4.0 * (Xs_i - share @ X[i])
+        out[r] = duchi(X[i] - tau * grad)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # similarity matrix from an edge list
 # ----------------------------------------------------------------------------

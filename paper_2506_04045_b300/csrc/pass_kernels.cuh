@@ -1,0 +1,702 @@
+// Fused FISTA pass for similarity-based fuzzy clustering on sm_103a.
+//
+// One launch of fista_pass_kernel is one iteration of the paper's parallel
+// FISTA (Algorithm 4) with its loss evaluation, restructured so that S is
+// streamed once per iteration:
+//
+//   z_i   = (S Xbar^{n-1})_i                       product with S (gather)
+//   p_i   = <xbar^{n-1}_i, z_i>                    trace term of f(Xbar^{n-1})
+//   y_i   = xbar^{n-1}_i + beta (xbar^{n-1}_i - xbar^{n-2}_i)       (X^n)
+//   (SY)_i = z_i + beta (z_i - z^{prev}_i)         linearity: S X^n without a
+//                                                  second product with S
+//   q_i   = y_i G(Y)                               G(Y) = Y^T Y = share^n
+//   xbar^n_i = P_simplex(y_i + 4 tau ((SY)_i - q_i))   gradient step of
+//                                                  Eq. "gradient_column"
+//   Gram partials of Xbar^n^T Xbar^n and Xbar^n^T Xbar^{n-1}
+//   ||y_i - xbar^n_i||^2                           projected-gradient norm
+//
+// G(Y) for the next pass is assembled by fold_kernel from the float64 Gram
+// matrices of the two newest iterates (Y = (1+beta) Xbar^n - beta Xbar^{n-1}
+// is a linear combination of them), which replaces Algorithm 4's second
+// "share"; f(Xbar^{n-1}) = ||S||^2 - 2 sum_i p_i + ||Xbar^{n-1 T} Xbar^{n-1}||^2
+// is the trace identity of Sect. 3 ("Loss Update").
+//
+// Layout: a "team" of T lanes owns one row; lane t holds VEC consecutive
+// features.  Teams of one warp take rows of similar degree (rows are visited in
+// degree order), so the gather loop is warp-uniform.  Rows are grouped into
+// tiles of R rows per block; after each tile the block adds the tile's outer
+// products into per-thread float32 Gram accumulators.  Rows of very high
+// degree are split into chunks whose partial products are computed by
+// heavy_kernel just before the pass.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "state.h"
+
+namespace fc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int KP>
+struct Lay {
+  static constexpr int VEC = KP < 4 ? KP : 4;      // features per lane
+  static constexpr int T = KP / VEC;                // lanes per team (row)
+  static constexpr int TPW = 32 / T;                // teams per warp
+  static constexpr int NT = KP >= 128 ? 512 : 256;  // threads per block
+  static constexpr int WARPS = NT / 32;
+  static constexpr int R = WARPS * TPW;             // rows per tile
+  static constexpr int NB = T > 8 ? T : 8;          // nonzeros per gather batch per team
+  static constexpr int PER = NB / T;                // (col, val) pairs each lane fetches per batch
+  static constexpr int E2 = KP * KP;
+  static constexpr int W = E2 / NT > 0 ? E2 / NT : 1;  // Gram entries per thread per matrix
+  static constexpr int OWN = E2 / W;                // threads owning distinct entries
+  static constexpr int GROUPS = NT / OWN;           // row groups splitting a tile
+  static_assert(GROUPS * OWN == NT, "bad Gram ownership");
+};
+
+struct PassArgs {
+  const int64_t* row_ptr;    // [n+1]
+  const int32_t* col;        // [nnz]
+  const void* val;           // [nnz] float32 (FP32) or bfloat16 (mixed)
+  const int32_t* order;      // rows in processing order (nullptr: identity)
+  const int64_t* cta_pos;    // [gridDim.x + 1] position ranges (nullptr: even split)
+  int64_t n_heavy;           // positions [0, n_heavy) are chunked rows
+  const int64_t* chunk_ptr;  // [n_heavy + 1]
+  const int64_t* chunk_e0;   // [n_chunks]
+  const int64_t* chunk_e1;   // [n_chunks]
+  int64_t n_chunks;
+  float* hv_part;            // [n_chunks][KP] partial products of chunked rows
+  float* X0;                 // iterate buffers, n x KP float32 (Xbar^j in X_{j&1})
+  float* X1;
+  __nv_bfloat16* XS0;        // bfloat16 gather copies (mixed precision)
+  __nv_bfloat16* XS1;
+  float* Zp;                 // n x KP: S Xbar^{pass-1}, replaced by S Xbar^{pass}
+  const float* Gy;           // KP x KP float32, G(Y) minus its mean entry
+  float* gram_part;          // [gridDim.x][2][KP][KP]
+  double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite
+  FistaState* st;
+  int64_t n;
+  int32_t k;
+  int32_t eval_sel;          // objective-only pass: buffer index to evaluate
+};
+
+template <bool MIXED>
+struct GatherT;
+template <>
+struct GatherT<false> {
+  using V = float;
+};
+template <>
+struct GatherT<true> {
+  using V = __nv_bfloat16;
+};
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Load VEC consecutive features of the gathered iterate at element offset off.
+template <int VEC, bool MIXED>
+__device__ __forceinline__ void load_feat(const void* Xg, int64_t off, float* out) {
+  if constexpr (!MIXED) {
+    const float* p = reinterpret_cast<const float*>(Xg) + off;
+    if constexpr (VEC == 4) {
+      float4 v = __ldg(reinterpret_cast<const float4*>(p));
+      out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else if constexpr (VEC == 2) {
+      float2 v = __ldg(reinterpret_cast<const float2*>(p));
+      out[0] = v.x; out[1] = v.y;
+    } else {
+      out[0] = __ldg(p);
+    }
+  } else {
+    const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(Xg) + off;
+    if constexpr (VEC == 4) {
+      uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+      __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&raw.x);
+      __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&raw.y);
+      float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
+    } else if constexpr (VEC == 2) {
+      unsigned raw = __ldg(reinterpret_cast<const unsigned*>(p));
+      float2 f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw));
+      out[0] = f.x; out[1] = f.y;
+    } else {
+      out[0] = __bfloat162float(p[0]);
+    }
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_row(const float* base, float* out) {
+  if constexpr (VEC == 4) {
+    float4 v = *reinterpret_cast<const float4*>(base);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else if constexpr (VEC == 2) {
+    float2 v = *reinterpret_cast<const float2*>(base);
+    out[0] = v.x; out[1] = v.y;
+  } else {
+    out[0] = base[0];
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_row(float* base, const float* v) {
+  if constexpr (VEC == 4) {
+    *reinterpret_cast<float4*>(base) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<float2*>(base) = make_float2(v[0], v[1]);
+  } else {
+    base[0] = v[0];
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* base, const float* v) {
+  if constexpr (VEC == 4) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<unsigned*>(&a);
+    raw.y = *reinterpret_cast<unsigned*>(&b);
+    *reinterpret_cast<uint2*>(base) = raw;
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<__nv_bfloat162*>(base) = __floats2bfloat162_rn(v[0], v[1]);
+  } else {
+    base[0] = __float2bfloat16_rn(v[0]);
+  }
+}
+
+// Sum over the T lanes of a team (teams are aligned groups of T lanes).
+template <int T>
+__device__ __forceinline__ float team_sum(float v) {
+#pragma unroll
+  for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// acc += sum_{e in [lo, hi)} val[e] * Xg[col[e], f0 .. f0+VEC).  `batches` must
+// be the same on every lane of the warp (the maximum over its teams).
+template <int KP, bool MIXED>
+__device__ __forceinline__ void gather(const int32_t* __restrict__ col, const void* __restrict__ valp,
+                                       const void* __restrict__ Xg, int64_t lo, int64_t hi, int batches,
+                                       int lt, int f0, float* acc) {
+  using L = Lay<KP>;
+  using VT = typename GatherT<MIXED>::V;
+  const VT* val = reinterpret_cast<const VT*>(valp);
+  for (int j = 0; j < batches; ++j) {
+    const int64_t e0 = lo + (int64_t)j * L::NB;
+    int ci[L::PER];
+    float cv[L::PER];
+#pragma unroll
+    for (int p = 0; p < L::PER; ++p) {
+      const int64_t e = e0 + lt + p * L::T;
+      const bool ok = e < hi;
+      ci[p] = ok ? __ldg(col + e) : 0;
+      cv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
+    }
+    float xv[L::NB][L::VEC];
+#pragma unroll
+    for (int u = 0; u < L::NB; ++u) {
+      const int c = L::T > 1 ? __shfl_sync(kFull, ci[u / L::T], u % L::T, L::T) : ci[u];
+      load_feat<L::VEC, MIXED>(Xg, (int64_t)c * KP + f0, xv[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < L::NB; ++u) {
+      const float v = L::T > 1 ? __shfl_sync(kFull, cv[u / L::T], u % L::T, L::T) : cv[u];
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) acc[q] = fmaf(v, xv[u][q], acc[q]);
+    }
+  }
+}
+
+// Euclidean projection of one row onto the unit simplex (the row's KP values
+// spread over the T lanes of a team, VEC per lane; features >= k are padding).
+// Michelot's active-set iteration: theta = (sum_{a in A} v_a - 1) / |A|, then
+// drop every a with v_a <= theta, until A is stable.  It reaches the same
+// threshold as Algorithm 1 (sort + cumulative sums) without sorting.  The
+// loop runs until every team of the warp is stable.
+template <int KP>
+__device__ __forceinline__ void project_simplex(const float* v, float* x, int f0, int k) {
+  using L = Lay<KP>;
+  bool act[L::VEC];
+  float s = 0.f, c = 0.f;
+#pragma unroll
+  for (int q = 0; q < L::VEC; ++q) {
+    act[q] = (f0 + q) < k;
+    s += act[q] ? v[q] : 0.f;
+    c += act[q] ? 1.f : 0.f;
+  }
+  s = team_sum<L::T>(s);
+  c = team_sum<L::T>(c);
+  float theta = (s - 1.0f) / c;
+  for (int it = 0; it <= KP; ++it) {
+    float s2 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) {
+      act[q] = act[q] && (v[q] > theta);
+      s2 += act[q] ? v[q] : 0.f;
+      c2 += act[q] ? 1.f : 0.f;
+    }
+    s2 = team_sum<L::T>(s2);
+    c2 = team_sum<L::T>(c2);
+    const bool changed = c2 != c;
+    if (changed) {
+      s = s2;
+      c = c2;
+      theta = (s - 1.0f) / c;
+    }
+    if (!__any_sync(kFull, changed)) break;
+  }
+#pragma unroll
+  for (int q = 0; q < L::VEC; ++q) x[q] = ((f0 + q) < k) ? fmaxf(v[q] - theta, 0.0f) : 0.0f;
+}
+
+template <int KP>
+__host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
+  using L = Lay<KP>;
+  // Gy (KP*KP) unless eval, then three R x KP tiles (xn, xp, ys)
+  return sizeof(float) * ((eval ? 0 : (size_t)L::E2) + 3 * (size_t)L::R * KP) + 64;
+}
+
+// One pass.  EVAL: objective-only (z = S X, p_i, Gram of X; no update).
+template <int KP, bool MIXED, bool EVAL>
+__global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
+  using L = Lay<KP>;
+  FistaState* st = a.st;
+  int64_t pass;
+  if constexpr (!EVAL) {
+    volatile FistaState* vs = st;
+    if (vs->done || vs->pass >= vs->limit) return;
+    pass = vs->pass;
+  } else {
+    pass = a.eval_sel;
+  }
+  const float beta = EVAL ? 0.f : (float)st->beta;
+  const float tau4 = EVAL ? 0.f : (float)(4.0 * st->tau);
+  const float* P = (pass & 1) ? a.X1 : a.X0;          // Xbar^{pass}
+  float* Q = (pass & 1) ? a.X0 : a.X1;                 // Xbar^{pass-1} in, Xbar^{pass+1} out
+  const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
+  __nv_bfloat16* XSo = (pass & 1) ? a.XS0 : a.XS1;
+
+  extern __shared__ __align__(16) float smem[];
+  float* Gs = smem;
+  float* xn_t = Gs + (EVAL ? 0 : L::E2);
+  float* xp_t = xn_t + L::R * KP;
+  float* ys = xp_t + L::R * KP;
+
+  const int tid = threadIdx.x;
+  if constexpr (!EVAL) {
+    for (int e = tid; e < L::E2; e += L::NT) Gs[e] = a.Gy[e];
+  }
+  __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tiw = lane / L::T, lt = lane % L::T;
+  const int team = warp * L::TPW + tiw;
+  const int f0 = lt * L::VEC;
+  const int k = a.k;
+
+  // Gram ownership: entries [ea*KP + eb0, +W) of each matrix, rows r = grp (mod GROUPS)
+  const int grp = tid / L::OWN;
+  const int eown = (tid % L::OWN) * L::W;
+  const int ea = eown / KP, eb0 = eown % KP;
+  float accA[L::W], accB[L::W];
+#pragma unroll
+  for (int w = 0; w < L::W; ++w) accA[w] = accB[w] = 0.f;
+
+  double tr_acc = 0.0, pg_acc = 0.0;
+  int bad = 0;
+
+  int64_t p0, p1;
+  if (a.cta_pos) {
+    p0 = a.cta_pos[blockIdx.x];
+    p1 = a.cta_pos[blockIdx.x + 1];
+  } else {
+    p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
+    p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  }
+
+  for (int64_t base = p0; base < p1; base += L::R) {
+    const int64_t pos = base + team;
+    const bool active = pos < p1;
+    const int64_t row = active ? (a.order ? (int64_t)a.order[pos] : pos) : 0;
+    float acc[L::VEC];
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+
+    int64_t lo = 0, hi = 0;
+    if (active && pos < a.n_heavy) {
+      // chunked row: sum the partial products in chunk order
+      const int64_t c0 = a.chunk_ptr[pos], c1 = a.chunk_ptr[pos + 1];
+      for (int64_t c = c0; c < c1; ++c) {
+        float pv[L::VEC];
+        load_row<L::VEC>(a.hv_part + c * KP + f0, pv);
+#pragma unroll
+        for (int q = 0; q < L::VEC; ++q) acc[q] += pv[q];
+      }
+    } else if (active) {
+      lo = a.row_ptr[row];
+      hi = a.row_ptr[row + 1];
+    }
+    const int nb = (int)((hi - lo + L::NB - 1) / L::NB);
+    const int batches = __reduce_max_sync(kFull, nb);
+    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+
+    float pv[L::VEC];
+    load_row<L::VEC>(P + row * KP + f0, pv);
+    float d = 0.f;
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) d = fmaf(pv[q], acc[q], d);
+    d = team_sum<L::T>(d);
+    if (active && lt == 0) tr_acc += (double)d;
+
+    if constexpr (!EVAL) {
+      float qv[L::VEC], zp[L::VEC], y[L::VEC], sy[L::VEC];
+      load_row<L::VEC>(Q + row * KP + f0, qv);
+      load_row<L::VEC>(a.Zp + row * KP + f0, zp);
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) {
+        y[q] = fmaf(beta, pv[q] - qv[q], pv[q]);
+        sy[q] = fmaf(beta, acc[q] - zp[q], acc[q]);
+      }
+      float* yrow = ys + team * KP;
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) yrow[f0 + q] = y[q];
+      __syncwarp();
+      // q_b = sum_a y_a G[a][b] for this lane's b in [f0, f0 + VEC)
+      float qq[L::VEC];
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) qq[q] = 0.f;
+#pragma unroll 4
+      for (int a4 = 0; a4 < KP; a4 += L::VEC) {
+        float ya[L::VEC];
+        load_row<L::VEC>(yrow + a4, ya);
+#pragma unroll
+        for (int aa = 0; aa < L::VEC; ++aa) {
+          float g[L::VEC];
+          load_row<L::VEC>(Gs + (a4 + aa) * KP + f0, g);
+#pragma unroll
+          for (int q = 0; q < L::VEC; ++q) qq[q] = fmaf(ya[aa], g[q], qq[q]);
+        }
+      }
+      float v[L::VEC], x[L::VEC];
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) v[q] = fmaf(tau4, sy[q] - qq[q], y[q]);
+      project_simplex<KP>(v, x, f0, k);
+      float pg = 0.f;
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) {
+        const float dd = y[q] - x[q];
+        pg = fmaf(dd, dd, pg);
+        if (!isfinite(x[q]) || !isfinite(acc[q])) bad = 1;
+      }
+      pg = team_sum<L::T>(pg);
+      if (active && lt == 0) pg_acc += (double)pg;
+      if (active) {
+        store_row<L::VEC>(Q + row * KP + f0, x);
+        store_row<L::VEC>(a.Zp + row * KP + f0, acc);
+        if constexpr (MIXED) store_row_bf16<L::VEC>(XSo + row * KP + f0, x);
+      }
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) {
+        xn_t[team * KP + f0 + q] = active ? x[q] : 0.f;
+        xp_t[team * KP + f0 + q] = active ? pv[q] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) {
+        xn_t[team * KP + f0 + q] = active ? pv[q] : 0.f;
+        if (active && !isfinite(acc[q])) bad = 1;
+      }
+    }
+    __syncthreads();
+    // Gram: A[ea][eb] += xn[r][ea] xn[r][eb];  B[ea][eb] += xn[r][ea] xp[r][eb]
+    for (int r = grp; r < L::R; r += L::GROUPS) {
+      const float xa = xn_t[r * KP + ea];
+      if constexpr (L::W % 4 == 0) {
+#pragma unroll
+        for (int w = 0; w < L::W; w += 4) {
+          const float4 xb = *reinterpret_cast<const float4*>(xn_t + r * KP + eb0 + w);
+          accA[w] = fmaf(xa, xb.x, accA[w]);
+          accA[w + 1] = fmaf(xa, xb.y, accA[w + 1]);
+          accA[w + 2] = fmaf(xa, xb.z, accA[w + 2]);
+          accA[w + 3] = fmaf(xa, xb.w, accA[w + 3]);
+          if constexpr (!EVAL) {
+            const float4 pb = *reinterpret_cast<const float4*>(xp_t + r * KP + eb0 + w);
+            accB[w] = fmaf(xa, pb.x, accB[w]);
+            accB[w + 1] = fmaf(xa, pb.y, accB[w + 1]);
+            accB[w + 2] = fmaf(xa, pb.z, accB[w + 2]);
+            accB[w + 3] = fmaf(xa, pb.w, accB[w + 3]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < L::W; ++w) {
+          accA[w] = fmaf(xa, xn_t[r * KP + eb0 + w], accA[w]);
+          if constexpr (!EVAL) accB[w] = fmaf(xa, xp_t[r * KP + eb0 + w], accB[w]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- block reductions (fixed order => bit-reproducible) ----
+  double* dred = reinterpret_cast<double*>(xn_t);  // reuse tile memory
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr_acc += __shfl_down_sync(kFull, tr_acc, o);
+    pg_acc += __shfl_down_sync(kFull, pg_acc, o);
+  }
+  bad = __reduce_or_sync(kFull, bad);
+  if (lane == 0) {
+    dred[warp * 3 + 0] = tr_acc;
+    dred[warp * 3 + 1] = pg_acc;
+    dred[warp * 3 + 2] = (double)bad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0, p = 0, b = 0;
+    for (int w = 0; w < L::WARPS; ++w) {
+      t += dred[w * 3 + 0];
+      p += dred[w * 3 + 1];
+      b += dred[w * 3 + 2];
+    }
+    a.sc_part[blockIdx.x * 4 + 0] = t;
+    a.sc_part[blockIdx.x * 4 + 1] = p;
+    a.sc_part[blockIdx.x * 4 + 2] = b;
+    a.sc_part[blockIdx.x * 4 + 3] = 0.0;
+  }
+  __syncthreads();
+  float* gout = a.gram_part + (size_t)blockIdx.x * 2 * L::E2;
+  if constexpr (L::GROUPS == 1) {
+#pragma unroll
+    for (int w = 0; w < L::W; ++w) {
+      gout[eown + w] = accA[w];
+      if constexpr (!EVAL) gout[L::E2 + eown + w] = accB[w];
+    }
+  } else {
+    float* gred = xn_t;  // GROUPS * E2 * 2 floats = NT * W * 2 <= 3 * R * KP
+#pragma unroll
+    for (int w = 0; w < L::W; ++w) {
+      gred[(grp * L::E2 + eown + w) * 2 + 0] = accA[w];
+      gred[(grp * L::E2 + eown + w) * 2 + 1] = accB[w];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int w = 0; w < L::W; ++w) {
+        float sa = 0.f, sb = 0.f;
+        for (int g = 0; g < L::GROUPS; ++g) {
+          sa += gred[(g * L::E2 + eown + w) * 2 + 0];
+          sb += gred[(g * L::E2 + eown + w) * 2 + 1];
+        }
+        gout[eown + w] = sa;
+        if constexpr (!EVAL) gout[L::E2 + eown + w] = sb;
+      }
+    }
+  }
+}
+
+// Partial products of chunked (very high degree) rows: hv_part[c] = sum over
+// chunk c's nonzeros of s_ij * xbar_j.  Teams stride over chunks in rounds so
+// that the gather stays warp-uniform.
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT) heavy_kernel(PassArgs a) {
+  using L = Lay<KP>;
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  const float* P = (pass & 1) ? a.X1 : a.X0;
+  const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tiw = lane / L::T, lt = lane % L::T, f0 = lt * L::VEC;
+  const int64_t teams = (int64_t)gridDim.x * L::R;
+  const int64_t gteam = (int64_t)blockIdx.x * L::R + warp * L::TPW + tiw;
+  const int64_t rounds = (a.n_chunks + teams - 1) / teams;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t c = gteam + r * teams;
+    const bool active = c < a.n_chunks;
+    const int64_t lo = active ? a.chunk_e0[c] : 0, hi = active ? a.chunk_e1[c] : 0;
+    float acc[L::VEC];
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+    const int nb = (int)((hi - lo + L::NB - 1) / L::NB);
+    const int batches = __reduce_max_sync(kFull, nb);
+    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+    if (active) store_row<L::VEC>(a.hv_part + c * KP + f0, acc);
+  }
+}
+
+struct FoldArgs {
+  FistaState* st;
+  const float* gram_part;   // [parts][2][KP][KP]
+  const double* sc_part;    // [parts][4]
+  int32_t parts;
+  int32_t eval;             // 1: objective-only pass (A only)
+  int32_t eval_init;        // 1: also seed the solver (A_0, Gy, gram2_cur)
+  int32_t pad_;
+  double* A0;               // Gram of Xbar^j in A_{j&1}, KP x KP float64
+  double* A1;
+  double* B;                // Xbar^{pass}^T Xbar^{pass-1}
+  double* Aeval;            // objective-only result
+  float* Gy;                // KP x KP float32 for the next pass
+};
+
+// Sums the per-block partials in block order (float64), evaluates the loss of
+// Xbar^{n-1}, applies the stop rule, advances t and the momentum factor, and
+// forms G(Y^{n+1}) = (1+b)^2 A_n - b(1+b)(B_n + B_n^T) + b^2 A_{n-1} minus its
+// mean entry (the mean shift leaves the projection unchanged because rows of
+// Y sum to one: P(v + c 1) = P(v)).
+template <int KP>
+__global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
+  constexpr int E2 = KP * KP;
+  FistaState* st = f.st;
+  volatile FistaState* vs = st;
+  if (!f.eval && (vs->done || vs->pass >= vs->limit)) return;
+  const int64_t pass = vs->pass;
+  const int64_t nnew = pass + 1;
+  const int tid = threadIdx.x;
+  const int nent = f.eval ? E2 : 2 * E2;
+  double* Adst = f.eval ? f.Aeval : ((nnew & 1) ? f.A1 : f.A0);
+  const int e = blockIdx.x * 256 + tid;
+  if (e < nent) {
+    double s = 0.0;
+    for (int c = 0; c < f.parts; ++c) s += (double)f.gram_part[(size_t)c * 2 * E2 + e];
+    if (e < E2) Adst[e] = s;
+    else f.B[e - E2] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ int is_last;
+  if (tid == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+
+  __shared__ double red[256];
+  __shared__ double sc[4];
+  const int k = st->k;
+  // ||A_new||_F^2 (fixed-order tree)
+  double part = 0.0;
+  for (int i = tid; i < E2; i += 256) {
+    const double v = __ldcg(Adst + i);
+    part += v * v;
+  }
+  red[tid] = part;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  const double gram2_new = red[0];
+  __syncthreads();
+  if (tid == 0) {
+    double tr = 0, pg = 0, bad = 0;
+    for (int c = 0; c < f.parts; ++c) {
+      tr += __ldcg(f.sc_part + c * 4 + 0);
+      pg += __ldcg(f.sc_part + c * 4 + 1);
+      bad += __ldcg(f.sc_part + c * 4 + 2);
+    }
+    double beta_next = 0.0;
+    if (f.eval) {
+      st->eval_trace = tr;
+      st->eval_gram2 = gram2_new;
+      st->eval_f = st->S2 - 2.0 * tr + gram2_new;
+      if (f.eval_init) {
+        st->gram2_cur = gram2_new;
+        st->beta = 0.0;
+      }
+    } else {
+      // loss of Xbar^{pass} (= Xbar^{n-1} for this pass n = pass + 1)
+      const double loss = st->S2 - 2.0 * tr + st->gram2_cur;
+      st->trace_last = tr;
+      st->gram2_last = st->gram2_cur;
+      st->loss_last = loss;
+      st->f_iter = pass;
+      const double r = sqrt(pg) / st->tau;
+      st->pg_last = r;
+      if (nnew == 1) st->pg_first = r;
+      int done = 0, status = 0;
+      int64_t out = nnew;
+      if (bad > 0.0 || !isfinite(loss)) {
+        done = 1;
+        status = 4;
+        out = pass;
+      } else if (st->stop_rule == 0) {
+        if (pass >= 1 && st->loss_prev - loss <= st->tol) {
+          done = 1;
+          out = pass;
+        }
+      } else if (st->stop_rule == 1) {
+        if (r <= st->tol * st->pg_first) done = 1;
+      } else if (st->stop_rule == 2) {
+        if (r <= st->tol) done = 1;
+      }
+      if (!done && nnew >= st->max_iter) {
+        done = 1;
+        status = 5;
+      }
+      st->loss_prev = loss;
+      st->gram2_cur = gram2_new;
+      const double t = st->t;
+      const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      beta_next = st->accel ? (t - 1.0) / t_next : 0.0;
+      st->t = t_next;
+      st->beta = beta_next;
+      st->out_iter = out;
+      st->status = status;
+      st->done = done;
+      st->pass = nnew;
+    }
+    sc[3] = beta_next;
+  }
+  __syncthreads();
+  // G(Y) for the next pass, then subtract its mean over the k x k block
+  if (!f.eval || f.eval_init) {
+    const double b = sc[3];
+    const double* An = f.eval ? f.Aeval : Adst;
+    const double* Ao = f.eval ? f.Aeval : ((nnew & 1) ? f.A0 : f.A1);
+    double msum = 0.0;
+    for (int i = tid; i < E2; i += 256) {
+      const int r = i / KP, c = i % KP;
+      if (r < k && c < k) {
+        double g;
+        if (f.eval) {
+          g = __ldcg(An + i);
+        } else {
+          const double bb = __ldcg(f.B + i) + __ldcg(f.B + c * KP + r);
+          g = (1.0 + b) * (1.0 + b) * __ldcg(An + i) - b * (1.0 + b) * bb + b * b * __ldcg(Ao + i);
+        }
+        msum += g;
+      }
+    }
+    red[tid] = msum;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const double mean = red[0] / ((double)k * (double)k);
+    for (int i = tid; i < E2; i += 256) {
+      const int r = i / KP, c = i % KP;
+      double g = 0.0;
+      if (r < k && c < k) {
+        if (f.eval) {
+          g = __ldcg(An + i);
+        } else {
+          const double bb = __ldcg(f.B + i) + __ldcg(f.B + c * KP + r);
+          g = (1.0 + b) * (1.0 + b) * __ldcg(An + i) - b * (1.0 + b) * bb + b * b * __ldcg(Ao + i);
+        }
+        g -= mean;
+      }
+      f.Gy[i] = (float)g;
+      if (f.eval && f.eval_init) f.A0[i] = __ldcg(An + i);
+    }
+    if (tid == 0) st->shift = mean;
+  }
+  if (tid == 0) st->ticket = 0u;
+}
+
+}  // namespace fc

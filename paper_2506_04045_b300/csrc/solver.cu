@@ -1,0 +1,877 @@
+// C ABI of the fuzzy-clustering solver: context set-up, the per-iteration
+// launch sequence captured in CUDA graphs, reports, checkpoints and the
+// standalone objective.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cub/cub.cuh>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "init_kernels.cuh"
+#include "pass_kernels.cuh"
+#include "solver_impl.h"
+#include "util.h"
+
+namespace fc {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+static int padded_k(int k) {
+  int kp = 2;
+  while (kp < k) kp <<= 1;
+  return kp;
+}
+
+static int grid_for(int64_t work, int threads = 256) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 65535LL * 8) b = 65535LL * 8;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// per-KP dispatch
+// ---------------------------------------------------------------------------
+template <int KP>
+struct KPOps {
+  using L = Lay<KP>;
+  static int rows_per_tile() { return L::R; }
+
+  template <bool MIXED, bool EVAL>
+  static cudaError_t setup_pass_attr() {
+    const size_t smem = pass_smem_bytes<KP>(EVAL);
+    return cudaFuncSetAttribute(fista_pass_kernel<KP, MIXED, EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  }
+  static cudaError_t setup_attrs() {
+    cudaError_t e;
+    if ((e = setup_pass_attr<false, false>()) != cudaSuccess) return e;
+    if ((e = setup_pass_attr<true, false>()) != cudaSuccess) return e;
+    if ((e = setup_pass_attr<false, true>()) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  static int occupancy(bool mixed) {
+    int occ = 0;
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (mixed)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fista_pass_kernel<KP, true, false>, L::NT, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fista_pass_kernel<KP, false, false>, L::NT, smem);
+    return occ < 1 ? 1 : occ;
+  }
+  static void launch_pass(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (mixed) fista_pass_kernel<KP, true, false><<<grid, L::NT, smem, s>>>(a);
+    else fista_pass_kernel<KP, false, false><<<grid, L::NT, smem, s>>>(a);
+  }
+  static void launch_eval(const PassArgs& a, int grid, cudaStream_t s) {
+    fista_pass_kernel<KP, false, true><<<grid, L::NT, pass_smem_bytes<KP>(true), s>>>(a);
+  }
+  static void launch_heavy(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+    if (mixed) heavy_kernel<KP, true><<<grid, L::NT, 0, s>>>(a);
+    else heavy_kernel<KP, false><<<grid, L::NT, 0, s>>>(a);
+  }
+  static void launch_fold(const FoldArgs& f, cudaStream_t s) {
+    const int nent = f.eval ? KP * KP : 2 * KP * KP;
+    fold_kernel<KP><<<(nent + 255) / 256, 256, 0, s>>>(f);
+  }
+};
+
+#define FC_DISPATCH(KPV, CALL)                        \
+  switch (KPV) {                                      \
+    case 2: { using Ops = KPOps<2>; CALL; } break;    \
+    case 4: { using Ops = KPOps<4>; CALL; } break;    \
+    case 8: { using Ops = KPOps<8>; CALL; } break;    \
+    case 16: { using Ops = KPOps<16>; CALL; } break;  \
+    case 32: { using Ops = KPOps<32>; CALL; } break;  \
+    case 64: { using Ops = KPOps<64>; CALL; } break;  \
+    default: { using Ops = KPOps<128>; CALL; } break; \
+  }
+
+static int kp_rows_per_tile(int KP) {
+  int r = 1;
+  FC_DISPATCH(KP, r = Ops::rows_per_tile());
+  return r;
+}
+static cudaError_t kp_setup_attrs(int KP) {
+  cudaError_t e = cudaSuccess;
+  FC_DISPATCH(KP, e = Ops::setup_attrs());
+  return e;
+}
+static int kp_occupancy(int KP, bool mixed) {
+  int o = 1;
+  FC_DISPATCH(KP, o = Ops::occupancy(mixed));
+  return o;
+}
+static void kp_launch_pass(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_pass(a, grid, mixed, s));
+}
+static void kp_launch_eval(int KP, const PassArgs& a, int grid, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_eval(a, grid, s));
+}
+static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, s));
+}
+static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+
+__global__ void set_limit_kernel(FistaState* st, int64_t iters) { st->limit = st->pass + iters; }
+
+// ---------------------------------------------------------------------------
+// CSR preparation shared by the solver and the standalone objective
+// ---------------------------------------------------------------------------
+static cluster_status prepare_rowptr(const cluster_csr* S, cudaStream_t s, const int64_t** rp_out,
+                                     int64_t** owned) {
+  *owned = nullptr;
+  if (S->index64) {
+    *rp_out = reinterpret_cast<const int64_t*>(S->row_ptr);
+    return CLUSTER_OK;
+  }
+  int64_t* rp = nullptr;
+  FC_CUDA(cudaMalloc(&rp, sizeof(int64_t) * (S->n + 1)));
+  rowptr32_to_64<<<grid_for(S->n + 1), 256, 0, s>>>(reinterpret_cast<const int32_t*>(S->row_ptr), rp, S->n + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(rp);
+    set_error("row_ptr conversion failed: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  *owned = rp;
+  *rp_out = rp;
+  return CLUSTER_OK;
+}
+
+static cluster_status check_csr_args(const cluster_csr* S, int32_t k) {
+  if (!S) FC_EINVAL("S is NULL");
+  if (S->n < 1) FC_EINVAL("n must be >= 1 (got %lld)", (long long)S->n);
+  if (S->n > 0x7fffffffLL) FC_EINVAL("n exceeds the int32 column range");
+  if (S->nnz < 0) FC_EINVAL("nnz must be >= 0");
+  if (k < 1 || k > 128) FC_EINVAL("k must be in [1, 128] (got %d)", k);
+  if (!S->row_ptr) FC_EINVAL("row_ptr is NULL");
+  if (S->nnz > 0 && (!S->col || !S->val)) FC_EINVAL("col/val are NULL");
+  return CLUSTER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context helpers
+// ---------------------------------------------------------------------------
+static void ctx_free(cluster_ctx* c) {
+  if (!c) return;
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
+                  c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
+                  c->A[1], c->B, c->Aeval, c->Gy, c->gram_part, c->sc_part, c->st};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+static PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.row_ptr = c->rp;
+  a.col = c->col;
+  a.val = (c->mixed && !eval_exact) ? (const void*)c->val16 : (const void*)c->val;
+  a.order = c->order;
+  a.cta_pos = c->cta_pos;
+  a.n_heavy = eval_exact ? 0 : c->n_heavy;
+  a.chunk_ptr = c->chunk_ptr;
+  a.chunk_e0 = c->chunk_e0;
+  a.chunk_e1 = c->chunk_e1;
+  a.n_chunks = c->n_chunks;
+  a.hv_part = c->hv_part;
+  a.X0 = c->X[0];
+  a.X1 = c->X[1];
+  a.XS0 = c->XS[0];
+  a.XS1 = c->XS[1];
+  a.Zp = c->Zp;
+  a.Gy = c->Gy;
+  a.gram_part = c->gram_part;
+  a.sc_part = c->sc_part;
+  a.st = c->st;
+  a.n = c->n;
+  a.k = c->k;
+  a.eval_sel = 0;
+  return a;
+}
+
+static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
+  FoldArgs f;
+  memset(&f, 0, sizeof(f));
+  f.st = c->st;
+  f.gram_part = c->gram_part;
+  f.sc_part = c->sc_part;
+  f.parts = c->parts;
+  f.eval = eval;
+  f.eval_init = eval_init;
+  f.A0 = c->A[0];
+  f.A1 = c->A[1];
+  f.B = c->B;
+  f.Aeval = c->Aeval;
+  f.Gy = c->Gy;
+  return f;
+}
+
+// Enqueue one iteration (heavy chunks, fused pass, fold).
+static void enqueue_pass(const cluster_ctx* c, cudaStream_t s) {
+  PassArgs a = make_pass_args(c, false);
+  if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, s);
+  kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
+  kp_launch_fold(c->KP, make_fold_args(c, 0, 0), s);
+}
+
+// Objective-only pass over iterate buffer `sel` (float32 master, float32 S).
+static void enqueue_eval(const cluster_ctx* c, int sel, int init, cudaStream_t s) {
+  PassArgs a = make_pass_args(c, true);
+  a.eval_sel = sel;
+  kp_launch_eval(c->KP, a, c->parts, s);
+  kp_launch_fold(c->KP, make_fold_args(c, 1, init), s);
+}
+
+static cluster_status read_state(cluster_ctx* c) {
+  FC_CUDA(cudaMemcpyAsync(&c->host_st, c->st, sizeof(FistaState), cudaMemcpyDeviceToHost, c->stream));
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  return CLUSTER_OK;
+}
+
+static void fill_report(const cluster_ctx* c, cluster_report* rep) {
+  if (!rep) return;
+  const FistaState& s = c->host_st;
+  rep->iters = s.pass;
+  rep->f_iter = s.f_iter;
+  rep->f = s.loss_last;
+  rep->trace_SU = s.trace_last;
+  rep->gram_fro2 = s.gram2_last;
+  rep->pg_norm = s.pg_last;
+  rep->tau = s.tau;
+  rep->L = s.L;
+  rep->out_iter = s.out_iter;
+  rep->done = s.done;
+  rep->status = s.status;
+}
+
+static cluster_status build_schedule(cluster_ctx* c) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  uint32_t *deg = nullptr, *sdeg = nullptr;
+  int32_t* iota = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0, tmp2 = 0;
+  int64_t *cost = nullptr, *prefix = nullptr, *hlo = nullptr;
+  unsigned long long* cnt = nullptr;
+  cluster_status st = CLUSTER_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+  };
+  cudaError_t e;
+  do {
+    if ((e = cudaMalloc(&deg, sizeof(uint32_t) * n)) != cudaSuccess) { fail(e, "alloc deg"); break; }
+    if ((e = cudaMalloc(&sdeg, sizeof(uint32_t) * n)) != cudaSuccess) { fail(e, "alloc sdeg"); break; }
+    if ((e = cudaMalloc(&iota, sizeof(int32_t) * n)) != cudaSuccess) { fail(e, "alloc iota"); break; }
+    if ((e = cudaMalloc(&c->order, sizeof(int32_t) * n)) != cudaSuccess) { fail(e, "alloc order"); break; }
+    degree_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, n, deg, iota);
+    // rows by degree, descending (stable radix sort: deterministic)
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, deg, sdeg, iota, c->order, (int)n, 0, 32, s);
+    if ((e = cudaMalloc(&cost, sizeof(int64_t) * n)) != cudaSuccess) { fail(e, "alloc cost"); break; }
+    if ((e = cudaMalloc(&prefix, sizeof(int64_t) * n)) != cudaSuccess) { fail(e, "alloc prefix"); break; }
+    cub::DeviceScan::InclusiveSum(nullptr, tmp2, cost, prefix, (int)n, s);
+    if (tmp2 > tmp_bytes) tmp_bytes = tmp2;
+    if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) { fail(e, "alloc sort temp"); break; }
+    if ((e = cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, sdeg, iota, c->order, (int)n, 0, 32,
+                                                       s)) != cudaSuccess) {
+      fail(e, "degree sort");
+      break;
+    }
+    // chunked ("heavy") rows: degree above H, split into chunks of H nonzeros
+    if ((e = cudaMalloc(&cnt, sizeof(unsigned long long))) != cudaSuccess) { fail(e, "alloc cnt"); break; }
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+    count_above_kernel<<<grid_for(n), 256, 0, s>>>(sdeg, n, (uint32_t)c->heavy_H, cnt);
+    unsigned long long nh = 0;
+    cudaMemcpyAsync(&nh, cnt, sizeof(nh), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "degree schedule"); break; }
+    c->n_heavy = (int64_t)nh;
+    if (nh > 0) {
+      std::vector<uint32_t> hdeg(nh);
+      std::vector<int64_t> hlo_h(nh);
+      if ((e = cudaMalloc(&hlo, sizeof(int64_t) * nh)) != cudaSuccess) { fail(e, "alloc hlo"); break; }
+      heavy_lo_kernel<<<grid_for((int64_t)nh), 256, 0, s>>>(c->rp, c->order, (int64_t)nh, hlo);
+      cudaMemcpyAsync(hdeg.data(), sdeg, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(hlo_h.data(), hlo, sizeof(int64_t) * nh, cudaMemcpyDeviceToHost, s);
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "heavy rows"); break; }
+      std::vector<int64_t> cptr(nh + 1), ce0, ce1;
+      cptr[0] = 0;
+      for (size_t p = 0; p < nh; ++p) {
+        const int64_t d = hdeg[p];
+        for (int64_t o = 0; o < d; o += c->heavy_H) {
+          ce0.push_back(hlo_h[p] + o);
+          ce1.push_back(hlo_h[p] + std::min<int64_t>(d, o + c->heavy_H));
+        }
+        cptr[p + 1] = (int64_t)ce0.size();
+      }
+      c->n_chunks = (int64_t)ce0.size();
+      if ((e = cudaMalloc(&c->chunk_ptr, sizeof(int64_t) * (nh + 1))) != cudaSuccess) { fail(e, "alloc chunks"); break; }
+      if ((e = cudaMalloc(&c->chunk_e0, sizeof(int64_t) * c->n_chunks)) != cudaSuccess) { fail(e, "alloc chunks"); break; }
+      if ((e = cudaMalloc(&c->chunk_e1, sizeof(int64_t) * c->n_chunks)) != cudaSuccess) { fail(e, "alloc chunks"); break; }
+      if ((e = cudaMalloc(&c->hv_part, sizeof(float) * c->n_chunks * c->KP)) != cudaSuccess) { fail(e, "alloc hv"); break; }
+      cudaMemcpyAsync(c->chunk_ptr, cptr.data(), sizeof(int64_t) * (nh + 1), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(c->chunk_e0, ce0.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(c->chunk_e1, ce1.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice, s);
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "upload chunks"); break; }
+    }
+    // cost-balanced position ranges, one per block
+    cost_kernel<<<grid_for(n), 256, 0, s>>>(sdeg, n, c->n_heavy, (uint32_t)c->heavy_H, c->row_cost, cost);
+    if ((e = cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, cost, prefix, (int)n, s)) != cudaSuccess) {
+      fail(e, "cost scan");
+      break;
+    }
+    if ((e = cudaMalloc(&c->cta_pos, sizeof(int64_t) * (c->parts + 1))) != cudaSuccess) { fail(e, "alloc cta_pos"); break; }
+    partition_kernel<<<(c->parts + 1 + 255) / 256, 256, 0, s>>>(prefix, n, c->parts, c->cta_pos);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "partition"); break; }
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "schedule kernels"); break; }
+  } while (0);
+  void* tmps[] = {deg, sdeg, iota, tmp, cost, prefix, hlo, cnt};
+  for (void* p : tmps)
+    if (p) cudaFree(p);
+  return st;
+}
+
+static cluster_status power_norm(cluster_ctx* c, double* out) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  double *x = nullptr, *y = nullptr, *part = nullptr;
+  const int nb = 256;
+  std::vector<double> hp(nb);
+  FC_CUDA(cudaMalloc(&x, sizeof(double) * n));
+  FC_CUDA(cudaMalloc(&y, sizeof(double) * n));
+  FC_CUDA(cudaMalloc(&part, sizeof(double) * nb));
+  auto dot = [&](const double* a, const double* b) {
+    dot_part_kernel<<<nb, 256, 0, s>>>(a, b, n, part);
+    cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    double t = 0;
+    for (double v : hp) t += v;
+    return t;
+  };
+  fill_start_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
+  scale_kernel<<<grid_for(n), 256, 0, s>>>(x, n, 1.0 / std::sqrt(dot(x, x)));
+  double lam = 0.0;
+  for (int it = 0; it < 1000; ++it) {
+    spmv_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, c->col, c->val, x, n, y);
+    const double nrm = std::sqrt(dot(y, y));
+    if (!(nrm > 0.0)) break;
+    scale_kernel<<<grid_for(n), 256, 0, s>>>(y, n, 1.0 / nrm);
+    std::swap(x, y);
+    const bool conv = it > 5 && std::fabs(nrm - lam) <= 1e-10 * nrm;
+    lam = nrm;
+    if (conv) break;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaFree(x);
+  cudaFree(y);
+  cudaFree(part);
+  if (e != cudaSuccess) {
+    set_error("power iteration: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  *out = lam;
+  return CLUSTER_OK;
+}
+
+static cluster_status capture_graph(cluster_ctx* c) {
+  cudaGraph_t g = nullptr;
+  FC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < c->graph_chunk; ++i) enqueue_pass(c, c->cap_stream);
+  FC_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error("graph instantiate: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  return CLUSTER_OK;
+}
+
+static cluster_status validate_inputs(cluster_ctx* c, const float* U0) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  int* derr = nullptr;
+  int herr = 0;
+  FC_CUDA(cudaMalloc(&derr, sizeof(int)));
+  cudaMemsetAsync(derr, 0, sizeof(int), s);
+  validate_rowptr_kernel<<<grid_for(n + 1), 256, 0, s>>>(c->rp, n, c->nnz, derr);
+  cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && herr == 0) {
+    validate_csr_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, c->col, c->val, n, 1, derr);
+    validate_u0_kernel<<<grid_for(n), 256, 0, s>>>(U0, n, c->k, derr);
+    cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+  }
+  if (e == cudaSuccess && herr == 0 && c->opt.validate >= 2) {
+    validate_sym_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, c->col, c->val, n, derr);
+    cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFree(derr);
+  if (e != cudaSuccess) {
+    set_error("validation: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  if (herr) {
+    set_error("invalid input (flags 0x%x):%s%s%s%s%s%s%s%s", herr, (herr & kErrRowPtr) ? " row_ptr" : "",
+              (herr & kErrColRange) ? " col-range" : "", (herr & kErrColOrder) ? " col-order" : "",
+              (herr & kErrNoDiag) ? " missing-diagonal" : "", (herr & kErrValue) ? " nonfinite-value" : "",
+              (herr & kErrAsym) ? " asymmetric" : "", (herr & kErrU0Range) ? " U0-negative-or-nonfinite" : "",
+              (herr & kErrU0Sum) ? " U0-row-sum" : "");
+    return CLUSTER_EINVAL;
+  }
+  return CLUSTER_OK;
+}
+
+static cluster_status sum_squares(const float* val, int64_t nnz, cudaStream_t s, double* out) {
+  *out = 0.0;
+  if (nnz <= 0) return CLUSTER_OK;
+  const int nb = 1024;
+  double* part = nullptr;
+  std::vector<double> hp(nb);
+  FC_CUDA(cudaMalloc(&part, sizeof(double) * nb));
+  sumsq_kernel<<<nb, 256, 0, s>>>(val, nnz, part);
+  cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  if (e != cudaSuccess) {
+    set_error("sum of squares: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  double t = 0.0;
+  for (double v : hp) t += v;
+  *out = t;
+  return CLUSTER_OK;
+}
+
+static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* optp,
+                                void* stream, cluster_ctx* c) {
+  FC_TRY(check_csr_args(S, k));
+  if (!U0) FC_EINVAL("U0 is NULL");
+  cluster_options opt;
+  if (optp) opt = *optp;
+  else cluster_options_default(&opt);
+  if (opt.precision != CLUSTER_FP32 && opt.precision != CLUSTER_MIXED_BF16)
+    FC_EINVAL("unknown precision %d", opt.precision);
+  if (opt.step_rule < 0 || opt.step_rule > 2) FC_EINVAL("unknown step rule %d", opt.step_rule);
+  if (opt.stop_rule < 0 || opt.stop_rule > 3) FC_EINVAL("unknown stop rule %d", opt.stop_rule);
+  if (opt.max_iter < 1) FC_EINVAL("max_iter must be >= 1");
+  if (!(opt.tau >= 0.0) || !std::isfinite(opt.tau)) FC_EINVAL("tau must be finite and >= 0");
+  if (opt.step_rule == CLUSTER_STEP_CONST && !(opt.tau > 0.0)) FC_EINVAL("constant step needs tau > 0");
+  if (!std::isfinite(opt.tol)) FC_EINVAL("tol must be finite");
+  if (opt.graph_chunk < 1) opt.graph_chunk = 16;
+  c->opt = opt;
+  c->stream = (cudaStream_t)stream;
+  c->n = S->n;
+  c->nnz = S->nnz;
+  c->k = k;
+  c->KP = padded_k(k);
+  c->mixed = opt.precision == CLUSTER_MIXED_BF16;
+  c->graph_chunk = opt.graph_chunk;
+  FC_CUDA(cudaGetDevice(&c->dev));
+  FC_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n, nnz = c->nnz;
+
+  // CSR: int64 row pointers always; copy col/val unless borrowed
+  FC_TRY(prepare_rowptr(S, s, &c->rp, &c->rp_owned));
+  if (!c->rp_owned && !opt.borrow) {
+    FC_CUDA(cudaMalloc(&c->rp_owned, sizeof(int64_t) * (n + 1)));
+    FC_CUDA(cudaMemcpyAsync(c->rp_owned, S->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    c->rp = c->rp_owned;
+  }
+  if (opt.borrow || nnz == 0) {
+    c->col = S->col;
+    c->val = S->val;
+  } else {
+    FC_CUDA(cudaMalloc(&c->col_owned, sizeof(int32_t) * nnz));
+    FC_CUDA(cudaMalloc(&c->val_owned, sizeof(float) * nnz));
+    FC_CUDA(cudaMemcpyAsync(c->col_owned, S->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
+    FC_CUDA(cudaMemcpyAsync(c->val_owned, S->val, sizeof(float) * nnz, cudaMemcpyDeviceToDevice, s));
+    c->col = c->col_owned;
+    c->val = c->val_owned;
+  }
+  if (opt.validate >= 1) FC_TRY(validate_inputs(c, U0));
+
+  // ||S||_F^2 in float64, step size
+  double S2 = 0.0;
+  FC_TRY(sum_squares(c->val, nnz, s, &S2));
+  double L = 0.0, tau = opt.tau;
+  if (opt.step_rule == CLUSTER_STEP_INV_L_FROB) {
+    L = 4.0 * std::sqrt(S2) + 12.0 * (double)n;
+    tau = (opt.tau > 0.0 ? opt.tau : 1.0) / L;
+  } else if (opt.step_rule == CLUSTER_STEP_INV_L_SPEC) {
+    double nrm = 0.0;
+    FC_TRY(power_norm(c, &nrm));
+    L = 4.0 * nrm + 12.0 * (double)n;
+    tau = (opt.tau > 0.0 ? opt.tau : 1.0) / L;
+  }
+
+  // mixed precision: bfloat16 copy of the values
+  if (c->mixed && nnz > 0) {
+    FC_CUDA(cudaMalloc(&c->val16, sizeof(__nv_bfloat16) * nnz));
+    to_bf16_kernel<<<grid_for(nnz), 256, 0, s>>>(c->val, nnz, c->val16);
+  }
+
+  // launch geometry: one block range per resident block
+  FC_CUDA(kp_setup_attrs(c->KP));
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int occ = kp_occupancy(c->KP, c->mixed);
+  const int R = kp_rows_per_tile(c->KP);
+  int64_t parts = (int64_t)sms * occ;
+  const int64_t tiles = (n + R - 1) / R;
+  if (parts > tiles) parts = tiles;
+  if (parts < 1) parts = 1;
+  c->parts = (int)parts;
+  c->heavy_grid = sms * occ;
+  // rows above H nonzeros (about 64 KB of gathered float32 data) are chunked
+  c->heavy_H = std::max<int64_t>(64, 16384 / c->KP);
+  c->row_cost = 6;
+  FC_TRY(build_schedule(c));
+
+  // iterate buffers and reductions
+  const size_t nk = (size_t)n * c->KP;
+  FC_CUDA(cudaMalloc(&c->X[0], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->X[1], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->Zp, sizeof(float) * nk));
+  FC_CUDA(cudaMemsetAsync(c->Zp, 0, sizeof(float) * nk, s));
+  if (c->mixed) {
+    FC_CUDA(cudaMalloc(&c->XS[0], sizeof(__nv_bfloat16) * nk));
+    FC_CUDA(cudaMalloc(&c->XS[1], sizeof(__nv_bfloat16) * nk));
+  }
+  const size_t e2 = (size_t)c->KP * c->KP;
+  FC_CUDA(cudaMalloc(&c->A[0], sizeof(double) * e2));
+  FC_CUDA(cudaMalloc(&c->A[1], sizeof(double) * e2));
+  FC_CUDA(cudaMalloc(&c->B, sizeof(double) * e2));
+  FC_CUDA(cudaMalloc(&c->Aeval, sizeof(double) * e2));
+  FC_CUDA(cudaMalloc(&c->Gy, sizeof(float) * e2));
+  FC_CUDA(cudaMemsetAsync(c->A[1], 0, sizeof(double) * e2, s));
+  FC_CUDA(cudaMemsetAsync(c->B, 0, sizeof(double) * e2, s));
+  FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * c->parts));
+  FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * c->parts));
+  FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
+
+  // Xbar^0 = U0 in buffer 0; buffer 1 starts as a copy (momentum is 0 for the first two passes)
+  pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U0, n, k, c->KP, c->X[0], c->X[1], c->XS[0], c->XS[1]);
+  FistaState& h = c->host_st;
+  memset(&h, 0, sizeof(h));
+  h.S2 = S2;
+  h.tau = tau;
+  h.L = L;
+  h.tol = opt.tol;
+  h.t = 1.0;
+  h.beta = 0.0;
+  h.max_iter = opt.max_iter;
+  h.f_iter = -1;
+  h.out_iter = 0;
+  h.stop_rule = opt.stop_rule;
+  h.accel = opt.accel ? 1 : 0;
+  h.k = k;
+  FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
+  // Gram of Xbar^0 and f(Xbar^0): seeds G(Y^1) = Xbar^0^T Xbar^0
+  enqueue_eval(c, 0, 1, s);
+  FC_CUDA(cudaGetLastError());
+  FC_TRY(read_state(c));
+  h = c->host_st;
+  h.loss_last = h.eval_f;
+  h.trace_last = h.eval_trace;
+  h.gram2_last = h.eval_gram2;
+  h.f_iter = 0;
+  FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
+  FC_CUDA(cudaStreamSynchronize(s));
+  FC_TRY(capture_graph(c));
+  return CLUSTER_OK;
+}
+
+static cluster_status finalize_loss(cluster_ctx* c) {
+  FistaState& h = c->host_st;
+  if (h.f_iter == h.out_iter || h.status == 4) return CLUSTER_OK;
+  enqueue_eval(c, (int)(h.out_iter & 1), 0, c->stream);
+  FC_CUDA(cudaGetLastError());
+  FC_TRY(read_state(c));
+  FistaState& g = c->host_st;
+  g.loss_last = g.eval_f;
+  g.trace_last = g.eval_trace;
+  g.gram2_last = g.eval_gram2;
+  g.f_iter = g.out_iter;
+  // keep the device copy in step so later reports agree
+  FC_CUDA(cudaMemcpyAsync(&c->st->loss_last, &g.loss_last, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  FC_CUDA(cudaMemcpyAsync(&c->st->trace_last, &g.trace_last, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  FC_CUDA(cudaMemcpyAsync(&c->st->gram2_last, &g.gram2_last, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  FC_CUDA(cudaMemcpyAsync(&c->st->f_iter, &g.f_iter, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  return CLUSTER_OK;
+}
+
+// checkpoint layout: header, FistaState, A0, A1, B (float64 KP^2 each), Gy, X0, X1, Zp [, XS0, XS1]
+struct StateHeader {
+  uint64_t magic;
+  int64_t n;
+  int32_t k, KP, mixed, pad;
+};
+static const uint64_t kStateMagic = 0x46434C5553543031ull;  // "FCLUST01"
+
+static size_t state_bytes(const cluster_ctx* c) {
+  const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
+  size_t b = sizeof(StateHeader) + sizeof(FistaState) + 3 * e2 * sizeof(double) + e2 * sizeof(float) +
+             3 * nk * sizeof(float);
+  if (c->mixed) b += 2 * nk * sizeof(__nv_bfloat16);
+  return b;
+}
+
+}  // namespace fc
+
+using namespace fc;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" void cluster_options_default(cluster_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = CLUSTER_FP32;
+  opt->step_rule = CLUSTER_STEP_INV_L_FROB;
+  opt->stop_rule = CLUSTER_STOP_LOSS;
+  opt->accel = 1;
+  opt->borrow = 0;
+  opt->validate = 1;
+  opt->tau = 1.0;
+  opt->tol = 0.0;
+  opt->max_iter = 1000;
+  opt->graph_chunk = 16;
+}
+
+extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
+
+extern "C" cluster_status cluster_init(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* opt,
+                                       void* stream, cluster_ctx** out) {
+  clear_error();
+  if (!out) FC_EINVAL("out is NULL");
+  *out = nullptr;
+  cluster_ctx* c = new (std::nothrow) cluster_ctx();
+  if (!c) {
+    set_error("out of host memory");
+    return CLUSTER_ENOMEM;
+  }
+  cluster_status st = init_impl(S, k, U0, opt, stream, c);
+  if (st != CLUSTER_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    ctx_free(c);
+    return st;
+  }
+  *out = c;
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_enqueue(cluster_ctx* c, int64_t iters) {
+  clear_error();
+  if (!c) FC_EINVAL("ctx is NULL");
+  if (iters < 0) FC_EINVAL("iters must be >= 0");
+  if (iters == 0) return CLUSTER_OK;
+  FC_CUDA(cudaSetDevice(c->dev));
+  set_limit_kernel<<<1, 1, 0, c->stream>>>(c->st, iters);
+  const int64_t reps = (iters + c->graph_chunk - 1) / c->graph_chunk;
+  for (int64_t r = 0; r < reps; ++r) FC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+  FC_CUDA(cudaGetLastError());
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_step(cluster_ctx* c, int64_t iters, cluster_report* rep) {
+  FC_TRY(cluster_enqueue(c, iters));
+  FC_TRY(read_state(c));
+  fill_report(c, rep);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_get_report(cluster_ctx* c, cluster_report* rep) {
+  clear_error();
+  if (!c) FC_EINVAL("ctx is NULL");
+  FC_TRY(read_state(c));
+  fill_report(c, rep);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_solve(cluster_ctx* c, cluster_report* rep) {
+  clear_error();
+  if (!c) FC_EINVAL("ctx is NULL");
+  FC_CUDA(cudaSetDevice(c->dev));
+  FC_TRY(read_state(c));
+  while (!c->host_st.done) {
+    const int64_t left = c->host_st.max_iter - c->host_st.pass;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(left, (int64_t)c->graph_chunk * 8));
+    FC_TRY(cluster_step(c, chunk, nullptr));
+  }
+  FC_TRY(finalize_loss(c));
+  fill_report(c, rep);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_get_U(cluster_ctx* c, float* U_out) {
+  clear_error();
+  if (!c || !U_out) FC_EINVAL("NULL argument");
+  FC_CUDA(cudaSetDevice(c->dev));
+  FC_TRY(read_state(c));
+  const float* X = c->X[c->host_st.out_iter & 1];
+  unpad_kernel<<<grid_for(c->n * c->k), 256, 0, c->stream>>>(X, c->n, c->k, c->KP, U_out);
+  FC_CUDA(cudaGetLastError());
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_state_size(cluster_ctx* c, size_t* bytes) {
+  clear_error();
+  if (!c || !bytes) FC_EINVAL("NULL argument");
+  *bytes = state_bytes(c);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_get_state(cluster_ctx* c, void* buf, size_t bytes) {
+  clear_error();
+  if (!c || !buf) FC_EINVAL("NULL argument");
+  if (bytes < state_bytes(c)) FC_EINVAL("state buffer too small (%zu < %zu)", bytes, state_bytes(c));
+  FC_CUDA(cudaSetDevice(c->dev));
+  char* p = (char*)buf;
+  StateHeader hd{kStateMagic, c->n, c->k, c->KP, c->mixed ? 1 : 0, 0};
+  memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
+  struct Seg {
+    const void* src;
+    size_t b;
+  } segs[] = {{c->st, sizeof(FistaState)}, {c->A[0], e2 * 8}, {c->A[1], e2 * 8}, {c->B, e2 * 8},
+              {c->Gy, e2 * 4},           {c->X[0], nk * 4}, {c->X[1], nk * 4}, {c->Zp, nk * 4},
+              {c->XS[0], nk * 2},        {c->XS[1], nk * 2}};
+  const int nseg = c->mixed ? 10 : 8;
+  for (int i = 0; i < nseg; ++i) {
+    FC_CUDA(cudaMemcpyAsync(p, segs[i].src, segs[i].b, cudaMemcpyDeviceToHost, c->stream));
+    p += segs[i].b;
+  }
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, size_t bytes) {
+  clear_error();
+  if (!c || !buf) FC_EINVAL("NULL argument");
+  if (bytes < state_bytes(c)) FC_EINVAL("state buffer too small");
+  FC_CUDA(cudaSetDevice(c->dev));
+  const char* p = (const char*)buf;
+  StateHeader hd;
+  memcpy(&hd, p, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.n != c->n || hd.k != c->k || hd.KP != c->KP || hd.mixed != (c->mixed ? 1 : 0))
+    FC_EINVAL("state does not match this context (n, k or precision differ)");
+  p += sizeof(hd);
+  FistaState fs;
+  memcpy(&fs, p, sizeof(fs));
+  fs.ticket = 0;
+  const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
+  struct Seg {
+    void* dst;
+    size_t b;
+  } segs[] = {{c->st, sizeof(FistaState)}, {c->A[0], e2 * 8}, {c->A[1], e2 * 8}, {c->B, e2 * 8},
+              {c->Gy, e2 * 4},           {c->X[0], nk * 4}, {c->X[1], nk * 4}, {c->Zp, nk * 4},
+              {c->XS[0], nk * 2},        {c->XS[1], nk * 2}};
+  const int nseg = c->mixed ? 10 : 8;
+  for (int i = 0; i < nseg; ++i) {
+    const void* src = (i == 0) ? (const void*)&fs : (const void*)p;
+    FC_CUDA(cudaMemcpyAsync(segs[i].dst, src, segs[i].b, cudaMemcpyHostToDevice, c->stream));
+    p += segs[i].b;
+  }
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  c->host_st = fs;
+  return CLUSTER_OK;
+}
+
+extern "C" void cluster_destroy(cluster_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  cudaStreamSynchronize(c->stream);
+  ctx_free(c);
+}
+
+// ---------------------------------------------------------------------------
+// standalone objective
+// ---------------------------------------------------------------------------
+extern "C" cluster_status cluster_objective(const cluster_csr* S, int32_t k, const float* U, void* stream,
+                                            double* f) {
+  clear_error();
+  FC_TRY(check_csr_args(S, k));
+  if (!U || !f) FC_EINVAL("NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = S->n, nnz = S->nnz;
+  cluster_ctx tmp;  // only the fields the objective pass reads
+  tmp.stream = s;
+  tmp.n = n;
+  tmp.k = k;
+  tmp.KP = padded_k(k);
+  tmp.mixed = false;
+  const int KP = tmp.KP;
+  int dev = 0;
+  FC_CUDA(cudaGetDevice(&dev));
+  FC_CUDA(kp_setup_attrs(KP));
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int R = kp_rows_per_tile(KP);
+  int64_t parts = (int64_t)sms * 2;
+  if (parts > (n + R - 1) / R) parts = (n + R - 1) / R;
+  if (parts < 1) parts = 1;
+  tmp.parts = (int)parts;
+  const size_t e2 = (size_t)KP * KP, nk = (size_t)n * KP;
+  int64_t* rp_owned = nullptr;
+  FC_TRY(prepare_rowptr(S, s, &tmp.rp, &rp_owned));
+  tmp.col = S->col;
+  tmp.val = S->val;
+  cluster_status st = CLUSTER_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&tmp.X[0], sizeof(float) * nk)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&tmp.Aeval, sizeof(double) * e2)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&tmp.gram_part, sizeof(float) * 2 * e2 * parts)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&tmp.sc_part, sizeof(double) * 4 * parts)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&tmp.st, sizeof(FistaState))) != cudaSuccess) break;
+    FistaState h;
+    memset(&h, 0, sizeof(h));
+    h.k = k;
+    st = sum_squares(S->val, nnz, s, &h.S2);
+    if (st != CLUSTER_OK) break;
+    cudaMemcpyAsync(tmp.st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U, n, k, KP, tmp.X[0], nullptr, nullptr, nullptr);
+    enqueue_eval(&tmp, 0, 0, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    FistaState out;
+    cudaMemcpyAsync(&out, tmp.st, sizeof(out), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    *f = out.eval_f;
+  } while (0);
+  if (e != cudaSuccess) {
+    set_error("cluster_objective: %s", cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+  }
+  void* bufs[] = {rp_owned, tmp.X[0], tmp.Aeval, tmp.gram_part, tmp.sc_part, tmp.st};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  return st;
+}

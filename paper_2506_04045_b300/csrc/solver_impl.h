@@ -1,0 +1,54 @@
+// Solver context (opaque to callers of cluster.h).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cluster.h"
+#include "pass_kernels.cuh"
+#include "state.h"
+
+struct cluster_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture the graph
+  cluster_options opt{};
+  int64_t n = 0, nnz = 0;
+  int k = 0, KP = 0;
+  bool mixed = false;
+  // S (int64 row pointers; col/val borrowed or owned)
+  const int64_t* rp = nullptr;
+  const int32_t* col = nullptr;
+  const float* val = nullptr;
+  int64_t* rp_owned = nullptr;
+  int32_t* col_owned = nullptr;
+  float* val_owned = nullptr;
+  __nv_bfloat16* val16 = nullptr;
+  // schedule: rows by degree, cost-balanced block ranges, chunked rows
+  int32_t* order = nullptr;
+  int64_t* cta_pos = nullptr;
+  int parts = 1;
+  int heavy_grid = 1;
+  int64_t heavy_H = 512;
+  int64_t row_cost = 6;
+  int64_t n_heavy = 0, n_chunks = 0;
+  int64_t* chunk_ptr = nullptr;
+  int64_t* chunk_e0 = nullptr;
+  int64_t* chunk_e1 = nullptr;
+  float* hv_part = nullptr;
+  // iterate state
+  float* X[2] = {nullptr, nullptr};
+  __nv_bfloat16* XS[2] = {nullptr, nullptr};
+  float* Zp = nullptr;
+  double* A[2] = {nullptr, nullptr};
+  double* B = nullptr;
+  double* Aeval = nullptr;
+  float* Gy = nullptr;
+  float* gram_part = nullptr;
+  double* sc_part = nullptr;
+  fc::FistaState* st = nullptr;
+  fc::FistaState host_st{};
+  // graph of graph_chunk passes
+  int graph_chunk = 16;
+  cudaGraphExec_t graph_exec = nullptr;
+};

@@ -328,3 +328,17 @@ def test_toy_scenario1_random_starts():
         assert c2 != c6
         assert r.U[1, c2] > 0.99 and r.U[5, c6] > 0.99
         assert abs(r.U[3, 0] - 0.5) < 0.05
+
+
+def test_step_rows_reproduces_fista_iterations():
+    # the per-article step used for sampled checks equals Algorithm 4's own iterations
+    S, U0 = _config1()
+    tau = 1.0 / oracle.lipschitz(S)
+    r = oracle.fista(S, U0, tau, max_iter=6, stop="none", keep_history=True)
+    betas = oracle.momentum_factors(6)
+    hist = [U0] + r.history                      # Xbar^0 .. Xbar^6
+    rows = list(range(0, 2000, 37))
+    for n in range(2, 7):                        # Xbar^n from Xbar^{n-1}, Xbar^{n-2}
+        got = oracle.fista_step_rows(S, hist[n - 1], hist[n - 2], betas[n - 1], tau, rows)
+        assert np.allclose(got, hist[n][rows], rtol=0, atol=1e-13)
+    assert betas[:2] == [0.0, 0.0] and 0 < betas[2] < betas[3] < 1
