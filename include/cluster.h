@@ -166,6 +166,28 @@ CLUSTER_API cluster_status cluster_step(cluster_ctx* ctx, int64_t iters, cluster
  * &rep) afterwards to synchronise and read the state. */
 CLUSTER_API cluster_status cluster_enqueue(cluster_ctx* ctx, int64_t iters);
 
+/* Per-kernel timing of the fused iteration, averaged over the launches of
+ * one cluster_enqueue_profiled call (milliseconds, CUDA events on the
+ * context's stream).  pass = the fused pass kernel, heavy = the kernel that
+ * computes the partial products of chunked high-degree rows (0 if none),
+ * fold = the float64 fold.  heavy_nnz is the number of nonzeros the heavy
+ * kernel streams per iteration (the pass kernel streams nnz - heavy_nnz). */
+typedef struct cluster_kernel_times {
+  double pass_ms;
+  double heavy_ms;
+  double fold_ms;
+  double total_ms;     /* first event to last event                            */
+  int64_t launches;    /* iterations timed                                     */
+  int64_t heavy_nnz;
+  int64_t heavy_rows;
+} cluster_kernel_times;
+
+/* Run `iters` iterations launched one kernel at a time (no graph) with CUDA
+ * events between the kernels, synchronise, and return the per-kernel
+ * averages.  Same kernels and arithmetic as cluster_step; for measurement. */
+CLUSTER_API cluster_status cluster_enqueue_profiled(cluster_ctx* ctx, int64_t iters,
+                                                    cluster_kernel_times* out);
+
 /* Iterate until the stop rule fires or max_iter is reached, then make sure
  * rep->f is the loss of the returned iterate (one extra objective pass if
  * needed).  Returns CLUSTER_OK; rep->status tells how the run ended. */

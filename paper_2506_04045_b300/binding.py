@@ -54,6 +54,15 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("pass_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double), ("fold_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("heavy_nnz", ctypes.c_int64),
+                ("heavy_rows", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "cluster_options_default": (None, [ctypes.POINTER(Options)]),
@@ -62,6 +71,7 @@ _SIGS = {
                                     ctypes.POINTER(_P)]),
     "cluster_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(Report)]),
     "cluster_enqueue": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cluster_enqueue_profiled": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(KernelTimes)]),
     "cluster_solve": (ctypes.c_int, [_P, ctypes.POINTER(Report)]),
     "cluster_get_report": (ctypes.c_int, [_P, ctypes.POINTER(Report)]),
     "cluster_get_U": (ctypes.c_int, [_P, _P]),
@@ -181,6 +191,11 @@ class Solver:
 
     def enqueue(self, iters: int) -> None:
         check(self._lib.cluster_enqueue(self._ctx, int(iters)))
+
+    def enqueue_profiled(self, iters: int) -> dict:
+        kt = KernelTimes()
+        check(self._lib.cluster_enqueue_profiled(self._ctx, int(iters), ctypes.byref(kt)))
+        return kt.as_dict()
 
     def solve(self) -> dict:
         rep = Report()

@@ -324,6 +324,7 @@ static cluster_status build_schedule(cluster_ctx* c) {
           ce1.push_back(hlo_h[p] + std::min<int64_t>(d, o + c->heavy_H));
         }
         cptr[p + 1] = (int64_t)ce0.size();
+        c->heavy_nnz += d;
       }
       c->n_chunks = (int64_t)ce0.size();
       if ((e = cudaMalloc(&c->chunk_ptr, sizeof(int64_t) * (nh + 1))) != cudaSuccess) { fail(e, "alloc chunks"); break; }
@@ -696,6 +697,56 @@ extern "C" cluster_status cluster_enqueue(cluster_ctx* c, int64_t iters) {
   const int64_t reps = (iters + c->graph_chunk - 1) / c->graph_chunk;
   for (int64_t r = 0; r < reps; ++r) FC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
   FC_CUDA(cudaGetLastError());
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters, cluster_kernel_times* out) {
+  clear_error();
+  if (!c || !out) FC_EINVAL("NULL argument");
+  if (iters < 1) FC_EINVAL("iters must be >= 1");
+  FC_CUDA(cudaSetDevice(c->dev));
+  memset(out, 0, sizeof(*out));
+  cudaStream_t s = c->stream;
+  std::vector<cudaEvent_t> ev((size_t)(4 * iters));
+  for (auto& e : ev) FC_CUDA(cudaEventCreate(&e));
+  set_limit_kernel<<<1, 1, 0, s>>>(c->st, iters);
+  PassArgs a = make_pass_args(c, false);
+  const FoldArgs f = make_fold_args(c, 0, 0);
+  for (int64_t i = 0; i < iters; ++i) {
+    cudaEvent_t* e = &ev[(size_t)(4 * i)];
+    cudaEventRecord(e[0], s);
+    if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, s);
+    cudaEventRecord(e[1], s);
+    kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
+    cudaEventRecord(e[2], s);
+    kp_launch_fold(c->KP, f, s);
+    cudaEventRecord(e[3], s);
+  }
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  double th = 0, tp = 0, tf = 0;
+  float ms = 0.f;
+  for (int64_t i = 0; i < iters && err == cudaSuccess; ++i) {
+    cudaEvent_t* e = &ev[(size_t)(4 * i)];
+    cudaEventElapsedTime(&ms, e[0], e[1]); th += ms;
+    cudaEventElapsedTime(&ms, e[1], e[2]); tp += ms;
+    cudaEventElapsedTime(&ms, e[2], e[3]); tf += ms;
+  }
+  if (err == cudaSuccess) {
+    cudaEventElapsedTime(&ms, ev.front(), ev.back());
+    out->total_ms = ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) {
+    set_error("profiled iterations: %s", cudaGetErrorString(err));
+    return CLUSTER_ECUDA;
+  }
+  out->pass_ms = tp / iters;
+  out->heavy_ms = th / iters;
+  out->fold_ms = tf / iters;
+  out->launches = iters;
+  out->heavy_rows = c->n_heavy;
+  out->heavy_nnz = c->heavy_nnz;
   return CLUSTER_OK;
 }
 

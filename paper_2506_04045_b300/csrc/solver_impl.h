@@ -31,7 +31,7 @@ struct cluster_ctx {
   int heavy_grid = 1;
   int64_t heavy_H = 512;
   int64_t row_cost = 6;
-  int64_t n_heavy = 0, n_chunks = 0;
+  int64_t n_heavy = 0, n_chunks = 0, heavy_nnz = 0;
   int64_t* chunk_ptr = nullptr;
   int64_t* chunk_e0 = nullptr;
   int64_t* chunk_e1 = nullptr;

@@ -93,14 +93,26 @@ class _NodeTables:
     theta_max: float
 
 
-def _node_tables(n: int, blocks: int, gamma: float, seed: int) -> _NodeTables:
-    """Per-node memberships and integer propensities, always built on the CPU."""
-    idx = torch.arange(n, dtype=torch.int64)
+def _node_tables(n: int, blocks: int, gamma: float, seed: int, device=None) -> _NodeTables:
+    """Per-node memberships and integer propensities.  The Pareto draw (the
+    only floating-point step) is always evaluated on the CPU; the integer
+    tables are built on ``device`` (integer results do not depend on it)."""
+    dev = _dev(device)
     B = blocks
-    nblk = 1 + below(seed, _S_NBLK, idx, 3)
-    nblk = torch.clamp(nblk, max=B)
+    # Pareto(alpha = gamma - 1, x_min = 1) propensities, capped at sqrt(sum)
+    alpha = gamma - 1.0
+    u = uniform01(seed, _S_THETA, torch.arange(n, dtype=torch.int64))
+    theta = torch.pow(u, -1.0 / alpha)
+    del u
+    cap = math.sqrt(float(theta.sum()))
+    theta = torch.clamp(theta, max=cap)
+    theta_max = float(theta.max())
+    w = torch.floor(theta * 65536.0).to(torch.int64).to(dev)
+    del theta
+    idx = torch.arange(n, dtype=torch.int64, device=dev)
+    nblk = torch.clamp(1 + below(seed, _S_NBLK, idx, 3), max=B)
     b0 = below(seed, _S_B0, idx, B)
-    blk = torch.zeros((n, 3), dtype=torch.int64)
+    blk = torch.zeros((n, 3), dtype=torch.int64, device=dev)
     blk[:, 0] = b0
     if B >= 2:
         off1 = 1 + below(seed, _S_B1, idx, B - 1)
@@ -109,30 +121,29 @@ def _node_tables(n: int, blocks: int, gamma: float, seed: int) -> _NodeTables:
             off2 = 1 + below(seed, _S_B2, idx, B - 2)
             off2 = torch.where(off2 >= off1, off2 + 1, off2)
             blk[:, 2] = (b0 + off2) % B
-    # Pareto(alpha = gamma - 1, x_min = 1) propensities, capped at sqrt(sum)
-    alpha = gamma - 1.0
-    u = uniform01(seed, _S_THETA, idx)
-    theta = torch.pow(u, -1.0 / alpha)
-    cap = math.sqrt(float(theta.sum()))
-    theta = torch.clamp(theta, max=cap)
-    w = torch.floor(theta * 65536.0).to(torch.int64)
+            del off2
+        del off1
+    del b0
     cdf = torch.cumsum(w, 0)
     total = int(cdf[-1])
     # memberships sorted by (block, node)
-    slot = torch.arange(3, dtype=torch.int64).unsqueeze(0).expand(n, 3)
+    slot = torch.arange(3, dtype=torch.int64, device=dev).unsqueeze(0).expand(n, 3)
     valid = slot < nblk.unsqueeze(1)
     mb = blk[valid]
     mn = idx.unsqueeze(1).expand(n, 3)[valid]
+    del valid, idx
     order = torch.argsort(mb * n + mn)
     mb, mn = mb[order], mn[order]
+    del order
     mem_cdf = torch.cumsum(w[mn], 0)
     counts = torch.bincount(mb, minlength=B)
+    del mb
     ends = torch.cumsum(counts, 0)
     starts = ends - counts
     blk_base = torch.where(starts > 0, mem_cdf[torch.clamp(starts - 1, min=0)], torch.zeros_like(starts))
     blk_end = torch.where(counts > 0, mem_cdf[torch.clamp(ends - 1, min=0)], blk_base)
     blk_w = blk_end - blk_base
-    return _NodeTables(n, nblk, blk, cdf, total, mem_cdf, mn, blk_base, blk_w, float(theta.max()))
+    return _NodeTables(n, nblk, blk, cdf, total, mem_cdf, mn, blk_base, blk_w, theta_max)
 
 
 def dcsbm_edges(n: int, blocks: int, mean_deg: float, seed: int, gamma: float = 2.5,
@@ -153,14 +164,9 @@ def dcsbm_edges(n: int, blocks: int, mean_deg: float, seed: int, gamma: float = 
     nonzeros.  Returned tensors are int64 on ``device``.
     """
     dev = _dev(device)
-    t = _node_tables(n, blocks, gamma, seed)
-    cdf = t.cdf.to(dev)
-    nblk = t.nblk.to(dev)
-    blk = t.blk.to(dev)
-    mem_cdf = t.mem_cdf.to(dev)
-    mem_node = t.mem_node.to(dev)
-    blk_base = t.blk_base.to(dev)
-    blk_w = t.blk_w.to(dev)
+    t = _node_tables(n, blocks, gamma, seed, dev)
+    cdf, nblk, blk, mem_cdf, mem_node, blk_base, blk_w = (
+        t.cdf, t.nblk, t.blk, t.mem_cdf, t.mem_node, t.blk_base, t.blk_w)
     E = int(round(n * (mean_deg - 1.0) / 2.0))
     thr_in = int(mu_in * (1 << 20))
     if relabel:
