@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: parallel FISTA iterations/s for fuzzy clustering at paper scale.
+
+Workload (default): a citation-like synthetic graph with n = 70,000,000
+articles, k = 32 clusters, power-law degrees (DC-SBM, exponent 2.5) and about
+2e9 nonzeros in S, drawn on the GPU from the seeded generator in synth/ (the
+paper's OpenAlex graph is not available; this stands in for its shape).  A
+step is one fused iteration of the solver.  Both arithmetic forms run on the
+same graph and start point: plain FP32 and mixed (bfloat16 gathers and S
+values, FP32 accumulation, FP64 scalars).  ``value`` is the mixed form's
+iterations/s; the FP32 form's rate and the objectives of both after the same
+number of iterations are reported beside it.
+
+Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1 under
+torch.distributed.run every rank solves its own instance (replicas, weak
+scaling).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PG iters/s, mixed vs FP32, at equal objective (n=70M,k=32); serving p99 latency"
+UNIT = "iter/s"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_fista_pass.json")
+PASS_SRC = os.path.join(ROOT, "paper_2506_04045_b300", "csrc", "pass_kernels.cuh")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--n", type=int, default=70_000_000)
+    p.add_argument("--k", type=int, default=32)
+    p.add_argument("--mean-deg", type=float, default=28.9)
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--forms", default="fp32,mixed")
+    p.add_argument("--cpu-sample-n", type=int, default=1_000_000)
+    p.add_argument("--cpu-iters", type=int, default=2)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (per iteration) of the fused pass
+# ---------------------------------------------------------------------------
+def alg_bytes(n, nnz, k, mixed, heavy_nnz=0):
+    """B_alg = row_ptr + (col + val) per nonzero + one gathered row per nonzero
+    (rounded up to 32-byte sectors) + the two previous iterates' own rows read
+    and the new row written (float32 master) [+ the bfloat16 gather copy
+    written in the mixed form].  Nonzeros of chunked rows are streamed by the
+    heavy kernel and excluded here when ``heavy_nnz`` is given."""
+    bg = 2 if mixed else 4
+    bv = 2 if mixed else 4
+    row = math.ceil(k * bg / 32) * 32
+    m = nnz - heavy_nnz
+    b = 8 * (n + 1) + m * (4 + bv) + m * row + 3 * n * k * 4
+    if mixed:
+        b += n * k * 2
+    return b
+
+
+def kernel_digest() -> str:
+    with open(PASS_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_for(form: str):
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_sha") != kernel_digest():
+        return None
+    ent = d.get(form)
+    return None if ent is None else ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same generator
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle on a bounded sample: an n = cpu_sample_n instance of the
+    same generator, timed per iteration and scaled by nnz to the full size."""
+
+    def __init__(self, args):
+        import numpy as np
+        import scipy.sparse as sp
+        import threadpoolctl
+
+        import oracle
+        import synth
+        self.args = args
+        spec = synth.GraphSpec("dcsbm", args.cpu_sample_n, args.k, args.seed, mean_deg=args.mean_deg)
+        rp, c, v = synth.make_graph(spec)
+        self.n = spec.n
+        self.S = sp.csr_matrix((v.numpy().astype(np.float64), c.numpy(), rp.numpy()), shape=(spec.n, spec.n))
+        self.U0 = synth.dirichlet_u0(spec.n, args.k, args.seed).numpy().astype(np.float64)
+        self.tau = 1.0 / oracle.lipschitz(self.S)
+        info = threadpoolctl.threadpool_info()
+        self.cores = max([d.get("num_threads", 1) for d in info] + [1])
+
+    def seconds(self, iters: int) -> float:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.fista(self.S, self.U0, self.tau, max_iter=iters, stop="none")
+        return time.perf_counter() - t0
+
+    def describe(self, iters_text: str, n_full_nnz: int, its: float) -> str:
+        return (f"FP64 oracle (Algorithm 4, two products with S per iteration), {iters_text} on an "
+                f"n={self.n:,} k={self.args.k} instance of the same generator (nnz={self.S.nnz:,}), "
+                f"{its:.4f} it/s there, scaled by nnz to the full workload ({n_full_nnz:,} nonzeros); "
+                f"sparse products single-threaded, dense BLAS on {self.cores} threads")
+
+
+def cpu_baseline(args, n_full_nnz):
+    o = OracleSample(args)
+    dt = o.seconds(args.cpu_iters)
+    its = args.cpu_iters / dt
+    return {"value": its * o.S.nnz / n_full_nnz, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+            "sample": o.describe(f"{args.cpu_iters} iterations", n_full_nnz, its)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    nnz_full = int(round(args.n * ((args.mean_deg - 1.0) * 0.99 + 1.0)))
+    o = OracleSample(args)
+    for _ in range(args.warmup):
+        o.seconds(1)
+    t = sum(o.seconds(1) for _ in range(args.steps))
+    per_step = t / args.steps
+    value = (1.0 / per_step) * o.S.nnz / nnz_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1000.0 * nnz_full / o.S.nnz,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"dcsbm citation-like graph n={args.n:,} k={args.k} (oracle sample)",
+                       "n": args.n, "k": args.k, "sample_n": o.n, "sample_nnz": int(o.S.nnz)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+                             "sample": o.describe("1 iteration per step", nnz_full, 1.0 / per_step)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2506_04045_b300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    pkg.load()
+    seed = args.seed + rank
+    t_gen = time.perf_counter()
+    spec = synth.GraphSpec("dcsbm", args.n, args.k, seed, mean_deg=args.mean_deg)
+    rp, col, val = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(args.n, args.k, seed, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_gen
+    n, k, nnz = args.n, args.k, int(col.numel())
+    deg = rp[1:] - rp[:-1]
+    max_deg = int(deg.max())
+    del deg
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+    hbm, peak_kind = peaks()
+    forms = [f for f in args.forms.split(",") if f]
+    res = {}
+    sampler_summary = {}
+    for form in forms:
+        mixed = form == "mixed"
+        s = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
+                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
+        s.step(W)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as cs:
+            e0.record(stream)
+            kt = s.enqueue_profiled(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(ms)
+        U = s.get_U()
+        f = pkg.objective(rp, col, val, U)
+        rep = s.report()
+        res[form] = {"ms_total": ms, "it_s": K / (ms / 1000.0), "kt": kt, "f": f, "iters": rep["iters"],
+                     "launches": 1 + K * (3 if kt["heavy_rows"] > 0 else 2)}
+        sampler_summary[form] = cs.summary()
+        s.close()
+        del s, U
+        torch.cuda.empty_cache()
+
+    head = "mixed" if "mixed" in res else forms[0]
+    r = res[head]
+    mixed = head == "mixed"
+    kt = r["kt"]
+    b_pass = alg_bytes(n, nnz, k, mixed, kt["heavy_nnz"])
+    b_iter = alg_bytes(n, nnz, k, mixed, 0)
+    achieved = b_pass / (kt["pass_ms"] / 1000.0) / 1e9
+    traffic = traffic_for(head)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": "fista_pass_kernel<32,%s,false>" % ("true" if mixed else "false"),
+            "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
+            "pass_ms": kt["pass_ms"], "heavy_ms": kt["heavy_ms"], "fold_ms": kt["fold_ms"],
+            "iteration_alg_bytes": b_iter,
+            "iteration_frac": b_iter / (r["ms_total"] / K / 1000.0) / 1e9 / hbm}
+    clocks = sampler_summary[head]
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        try:
+            e2e = run_e2e(args, pkg, rp, col, val, U0, head, K, barrier, max_over_ranks)
+        except Exception as exc:  # e.g. pinned host memory unavailable
+            e2e = {"value": None, "unit": UNIT, "error": f"{type(exc).__name__}: {exc}"[:300]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline(args, nnz)
+        except Exception as exc:
+            cpu = {"value": None, "unit": UNIT, "kind": "oracle", "error": str(exc)[:200]}
+
+    value = sum_over_ranks(dist, r["it_s"] if ws == 1 else K / (r["ms_total"] / 1000.0), ws)
+    eq = None
+    if "fp32" in res and "mixed" in res:
+        eq = res["mixed"]["f"] <= res["fp32"]["f"] * (1 + 1e-5)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": r["ms_total"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32" if mixed else "f32", "data": "synthetic",
+        "config": {"workload": f"dcsbm citation-like graph n={n:,} k={k} nnz={nnz:,} (power-law degrees, "
+                               f"exponent 2.5, unit diagonal, weights in (0,1]), Dirichlet(1) start, step 1/L",
+                   "n": n, "k": k, "nnz": nnz, "max_degree": max_deg, "seed": args.seed,
+                   "l2": "inputs larger than L2 (S 16 GB, iterate 9 GB); no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "gen_seconds": round(gen_s, 1)},
+        "forms": {f: {"it_s": res[f]["it_s"], "ms_per_step": res[f]["ms_total"] / K, "objective": res[f]["f"],
+                      "pass_ms": res[f]["kt"]["pass_ms"], "heavy_ms": res[f]["kt"]["heavy_ms"],
+                      "fold_ms": res[f]["kt"]["fold_ms"], "iters_done": res[f]["iters"],
+                      "clocks": sampler_summary[f]} for f in res},
+        "equal_objective": eq,
+        "mixed_over_fp32": (res["mixed"]["it_s"] / res["fp32"]["it_s"]) if eq is not None else None,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": r["launches"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def sum_over_ranks(dist, x, ws):
+    if dist is None or ws == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
+    """Host CSR and start point (pinned) -> device copies -> cluster_init ->
+    K iterations, reading the loss back after each -> U copied to the host."""
+    import torch
+    h_rp = torch.empty(rp.shape, dtype=rp.dtype, pin_memory=True)
+    h_col = torch.empty(col.shape, dtype=col.dtype, pin_memory=True)
+    h_val = torch.empty(val.shape, dtype=val.dtype, pin_memory=True)
+    h_U0 = torch.empty(U0.shape, dtype=U0.dtype, pin_memory=True)
+    h_U = torch.empty(U0.shape, dtype=U0.dtype, pin_memory=True)
+    for h, d in ((h_rp, rp), (h_col, col), (h_val, val), (h_U0, U0)):
+        h.copy_(d)
+    d_rp, d_col, d_val, d_U0 = torch.empty_like(rp), torch.empty_like(col), torch.empty_like(val), torch.empty_like(U0)
+    mixed = form == "mixed"
+    stream = torch.cuda.current_stream()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for h, d in ((h_rp, d_rp), (h_col, d_col), (h_val, d_val), (h_U0, d_U0)):
+        d.copy_(h, non_blocking=True)
+    s = pkg.Solver(d_rp, d_col, d_val, d_U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
+                   precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
+    losses = []
+    for _ in range(K):
+        losses.append(s.step(1)["f"])
+    U = s.get_U()
+    h_U.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    s.close()
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_col, h_val, h_U0))
+    d2h = h_U.numel() * h_U.element_size() + K * 8
+    return {"value": K / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+            "d2h_bytes_per_step": d2h / K, "seconds": ms / 1000.0,
+            "note": "one solve: H2D of S and U0, cluster_init, K iterations each reading the loss, D2H of U"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_native(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()
