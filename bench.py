@@ -162,6 +162,19 @@ def traffic_for(form: str):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same generator
 # ---------------------------------------------------------------------------
+def blas_threads() -> int:
+    """Threads the oracle's dense BLAS calls use (its sparse products use one)."""
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([d.get("num_threads", 1) for d in info] + [1])
+    except ImportError:
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            if os.environ.get(var, "").isdigit():
+                return int(os.environ[var])
+        return os.cpu_count() or 1
+
+
 class OracleSample:
     """The FP64 oracle on a bounded sample: an n = cpu_sample_n instance of the
     same generator, timed per iteration and scaled by nnz to the full size."""
@@ -169,8 +182,6 @@ class OracleSample:
     def __init__(self, args):
         import numpy as np
         import scipy.sparse as sp
-        import threadpoolctl
-
         import oracle
         import synth
         self.args = args
@@ -180,8 +191,7 @@ class OracleSample:
         self.S = sp.csr_matrix((v.numpy().astype(np.float64), c.numpy(), rp.numpy()), shape=(spec.n, spec.n))
         self.U0 = synth.dirichlet_u0(spec.n, args.k, args.seed).numpy().astype(np.float64)
         self.tau = 1.0 / oracle.lipschitz(self.S)
-        info = threadpoolctl.threadpool_info()
-        self.cores = max([d.get("num_threads", 1) for d in info] + [1])
+        self.cores = blas_threads()
 
     def seconds(self, iters: int) -> float:
         import oracle
@@ -260,6 +270,7 @@ def run_native(args, ws, rank, local):
     rp, col, val = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(args.n, args.k, seed, device="cuda")
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t_gen
     n, k, nnz = args.n, args.k, int(col.numel())
     deg = rp[1:] - rp[:-1]

@@ -12,20 +12,22 @@
 //   q_i   = y_i G(Y)                               G(Y) = Y^T Y = share^n
 //   xbar^n_i = P_simplex(y_i + 4 tau ((SY)_i - q_i))   gradient step of
 //                                                  Eq. "gradient_column"
-//   Gram partials of Xbar^n^T Xbar^n and Xbar^n^T Xbar^{n-1}
+//   Gram partials of Xbar^n^T Xbar^n (for the loss) and of Y^{n+1}^T Y^{n+1},
+//   where y^{n+1}_i = xbar^n_i + beta_{n+1} (xbar^n_i - xbar^{n-1}_i) is the
+//   next pass's extrapolated row: the momentum schedule t_n does not depend
+//   on the data, so beta_{n+1} is known one pass ahead
 //   ||y_i - xbar^n_i||^2                           projected-gradient norm
 //
-// G(Y) for the next pass is assembled by fold_kernel from the float64 Gram
-// matrices of the two newest iterates (Y = (1+beta) Xbar^n - beta Xbar^{n-1}
-// is a linear combination of them), which replaces Algorithm 4's second
-// "share"; f(Xbar^{n-1}) = ||S||^2 - 2 sum_i p_i + ||Xbar^{n-1 T} Xbar^{n-1}||^2
-// is the trace identity of Sect. 3 ("Loss Update").
+// fold_kernel sums the Gram partials in float64 and hands G(Y^{n+1}) (the
+// "share" of the next iteration of Algorithm 4) to the next pass;
+// f(Xbar^{n-1}) = ||S||^2 - 2 sum_i p_i + ||Xbar^{n-1 T} Xbar^{n-1}||^2 is the
+// trace identity of Sect. 3 ("Loss Update").
 //
 // Layout: a "team" of T lanes owns one row; lane t holds VEC consecutive
 // features.  Teams of one warp take rows of similar degree (rows are visited in
 // degree order), so the gather loop is warp-uniform.  Rows are grouped into
 // tiles of R rows per block; after each tile the block adds the tile's outer
-// products into per-thread float32 Gram accumulators.  Rows of very high
+// products into per-thread float32 Gram accumulators (upper blocks only).  Rows of very high
 // degree are split into chunks whose partial products are computed by
 // heavy_kernel just before the pass.
 #pragma once
@@ -50,11 +52,40 @@ struct Lay {
   static constexpr int NB = T > 8 ? T : 8;          // nonzeros per gather batch per team
   static constexpr int PER = NB / T;                // (col, val) pairs each lane fetches per batch
   static constexpr int E2 = KP * KP;
-  static constexpr int W = E2 / NT > 0 ? E2 / NT : 1;  // Gram entries per thread per matrix
-  static constexpr int OWN = E2 / W;                // threads owning distinct entries
-  static constexpr int GROUPS = NT / OWN;           // row groups splitting a tile
-  static_assert(GROUPS * OWN == NT, "bad Gram ownership");
+  // resident blocks per SM the register budget is sized for
+  static constexpr int MINB = KP <= 4 ? 2 : (KP == 8 ? 3 : (KP <= 32 ? 4 : (KP == 64 ? 2 : 1)));
 };
+
+// Symmetric Gram accumulation: the KP x KP matrix is cut into BS x BS blocks
+// and only blocks (I, J) with I <= J are accumulated ("tasks"); the fold
+// mirrors them.  Two matrices per pass (Gram of Xbar^n and of Y^{n+1}), one in
+// an objective-only pass.  Threads take one task each and split the tile's
+// rows into GROUPS interleaved groups (or several tasks each when there are
+// more tasks than threads).
+template <int KP, bool EVAL>
+struct GramLay {
+  static constexpr int NT = Lay<KP>::NT;
+  static constexpr int BS = KP < 4 ? KP : 4;
+  static constexpr int NB1 = KP / BS;
+  static constexpr int NBLK = NB1 * (NB1 + 1) / 2;
+  static constexpr int MATS = EVAL ? 1 : 2;
+  static constexpr int TASKS = MATS * NBLK;
+  static constexpr int TPT = TASKS <= NT ? 1 : (TASKS + NT - 1) / NT;
+  static constexpr int GROUPS = TASKS <= NT ? NT / TASKS : 1;
+  static constexpr int ACTIVE = TASKS <= NT ? GROUPS * TASKS : NT;
+};
+
+// Task t of a GramLay -> (matrix m, block row I, block column J >= I).
+__device__ __forceinline__ void gram_task(int t, int nblk, int nb1, int& m, int& I, int& J) {
+  m = t / nblk;
+  int bi = t % nblk;
+  I = 0;
+  while (bi >= nb1 - I) {
+    bi -= nb1 - I;
+    ++I;
+  }
+  J = I + bi;
+}
 
 struct PassArgs {
   const int64_t* row_ptr;    // [n+1]
@@ -256,13 +287,17 @@ __device__ __forceinline__ void project_simplex(const float* v, float* x, int f0
 template <int KP>
 __host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
   using L = Lay<KP>;
-  // Gy (KP*KP) unless eval, then three R x KP tiles (xn, xp, ys)
-  return sizeof(float) * ((eval ? 0 : (size_t)L::E2) + 3 * (size_t)L::R * KP) + 64;
+  // Gy (KP*KP) unless eval, then three R x KP tiles (xn, yn, ys), which the
+  // end-of-kernel Gram group reduction reuses
+  const size_t tiles = 3 * (size_t)L::R * KP;
+  const size_t red = eval ? (size_t)GramLay<KP, true>::ACTIVE * GramLay<KP, true>::BS * GramLay<KP, true>::BS
+                          : (size_t)GramLay<KP, false>::ACTIVE * GramLay<KP, false>::BS * GramLay<KP, false>::BS;
+  return sizeof(float) * ((eval ? 0 : (size_t)L::E2) + (tiles > red ? tiles : red)) + 64;
 }
 
 // One pass.  EVAL: objective-only (z = S X, p_i, Gram of X; no update).
 template <int KP, bool MIXED, bool EVAL>
-__global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(PassArgs a) {
   using L = Lay<KP>;
   FistaState* st = a.st;
   int64_t pass;
@@ -274,6 +309,7 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
     pass = a.eval_sel;
   }
   const float beta = EVAL ? 0.f : (float)st->beta;
+  const float beta_next = EVAL ? 0.f : (float)st->beta_next;
   const float tau4 = EVAL ? 0.f : (float)(4.0 * st->tau);
   const float* P = (pass & 1) ? a.X1 : a.X0;          // Xbar^{pass}
   float* Q = (pass & 1) ? a.X0 : a.X1;                 // Xbar^{pass-1} in, Xbar^{pass+1} out
@@ -283,8 +319,8 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
   extern __shared__ __align__(16) float smem[];
   float* Gs = smem;
   float* xn_t = Gs + (EVAL ? 0 : L::E2);
-  float* xp_t = xn_t + L::R * KP;
-  float* ys = xp_t + L::R * KP;
+  float* yn_t = xn_t + L::R * KP;
+  float* ys = yn_t + L::R * KP;
 
   const int tid = threadIdx.x;
   if constexpr (!EVAL) {
@@ -298,13 +334,25 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
   const int f0 = lt * L::VEC;
   const int k = a.k;
 
-  // Gram ownership: entries [ea*KP + eb0, +W) of each matrix, rows r = grp (mod GROUPS)
-  const int grp = tid / L::OWN;
-  const int eown = (tid % L::OWN) * L::W;
-  const int ea = eown / KP, eb0 = eown % KP;
-  float accA[L::W], accB[L::W];
+  // Gram tasks of this thread (see GramLay)
+  using G = GramLay<KP, EVAL>;
+  constexpr int BS = G::BS;
+  const int ggrp = (G::TASKS <= L::NT) ? tid / G::TASKS : 0;
+  const bool gact = ggrp < G::GROUPS;
+  int gI[G::TPT], gJ[G::TPT], gM[G::TPT], gT[G::TPT];
+  bool gOn[G::TPT];
 #pragma unroll
-  for (int w = 0; w < L::W; ++w) accA[w] = accB[w] = 0.f;
+  for (int j = 0; j < G::TPT; ++j) {
+    const int t = (G::TASKS <= L::NT) ? tid % G::TASKS : tid + j * L::NT;
+    gT[j] = t;
+    gOn[j] = gact && t < G::TASKS;
+    gram_task(gOn[j] ? t : 0, G::NBLK, G::NB1, gM[j], gI[j], gJ[j]);
+  }
+  float gacc[G::TPT][BS * BS];
+#pragma unroll
+  for (int j = 0; j < G::TPT; ++j)
+#pragma unroll
+    for (int q = 0; q < BS * BS; ++q) gacc[j][q] = 0.f;
 
   double tr_acc = 0.0, pg_acc = 0.0;
   int bad = 0;
@@ -399,10 +447,12 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
         store_row<L::VEC>(a.Zp + row * KP + f0, acc);
         if constexpr (MIXED) store_row_bf16<L::VEC>(XSo + row * KP + f0, x);
       }
+      // next pass's extrapolated row y^{n+1} = xbar^n + beta_{n+1} (xbar^n - xbar^{n-1}),
+      // formed exactly as the next pass will form it, feeds G(Y^{n+1})
 #pragma unroll
       for (int q = 0; q < L::VEC; ++q) {
         xn_t[team * KP + f0 + q] = active ? x[q] : 0.f;
-        xp_t[team * KP + f0 + q] = active ? pv[q] : 0.f;
+        yn_t[team * KP + f0 + q] = active ? fmaf(beta_next, x[q] - pv[q], x[q]) : 0.f;
       }
     } else {
 #pragma unroll
@@ -412,30 +462,20 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
       }
     }
     __syncthreads();
-    // Gram: A[ea][eb] += xn[r][ea] xn[r][eb];  B[ea][eb] += xn[r][ea] xp[r][eb]
-    for (int r = grp; r < L::R; r += L::GROUPS) {
-      const float xa = xn_t[r * KP + ea];
-      if constexpr (L::W % 4 == 0) {
+    // symmetric Gram blocks: M[I-block][J-block] += m_r[I-block] (x) m_r[J-block]
+    if (gact) {
+      for (int r = ggrp; r < L::R; r += G::GROUPS) {
 #pragma unroll
-        for (int w = 0; w < L::W; w += 4) {
-          const float4 xb = *reinterpret_cast<const float4*>(xn_t + r * KP + eb0 + w);
-          accA[w] = fmaf(xa, xb.x, accA[w]);
-          accA[w + 1] = fmaf(xa, xb.y, accA[w + 1]);
-          accA[w + 2] = fmaf(xa, xb.z, accA[w + 2]);
-          accA[w + 3] = fmaf(xa, xb.w, accA[w + 3]);
-          if constexpr (!EVAL) {
-            const float4 pb = *reinterpret_cast<const float4*>(xp_t + r * KP + eb0 + w);
-            accB[w] = fmaf(xa, pb.x, accB[w]);
-            accB[w + 1] = fmaf(xa, pb.y, accB[w + 1]);
-            accB[w + 2] = fmaf(xa, pb.z, accB[w + 2]);
-            accB[w + 3] = fmaf(xa, pb.w, accB[w + 3]);
-          }
-        }
-      } else {
+        for (int j = 0; j < G::TPT; ++j) {
+          if (!gOn[j]) continue;
+          const float* src = (gM[j] ? yn_t : xn_t) + r * KP;
+          float xa[BS], xb[BS];
+          load_row<BS>(src + gI[j] * BS, xa);
+          load_row<BS>(src + gJ[j] * BS, xb);
 #pragma unroll
-        for (int w = 0; w < L::W; ++w) {
-          accA[w] = fmaf(xa, xn_t[r * KP + eb0 + w], accA[w]);
-          if constexpr (!EVAL) accB[w] = fmaf(xa, xp_t[r * KP + eb0 + w], accB[w]);
+          for (int p = 0; p < BS; ++p)
+#pragma unroll
+            for (int q = 0; q < BS; ++q) gacc[j][p * BS + q] = fmaf(xa[p], xb[q], gacc[j][p * BS + q]);
         }
       }
     }
@@ -470,44 +510,51 @@ __global__ void __launch_bounds__(Lay<KP>::NT) fista_pass_kernel(PassArgs a) {
   }
   __syncthreads();
   float* gout = a.gram_part + (size_t)blockIdx.x * 2 * L::E2;
-  if constexpr (L::GROUPS == 1) {
+  if constexpr (G::GROUPS == 1) {
 #pragma unroll
-    for (int w = 0; w < L::W; ++w) {
-      gout[eown + w] = accA[w];
-      if constexpr (!EVAL) gout[L::E2 + eown + w] = accB[w];
+    for (int j = 0; j < G::TPT; ++j) {
+      if (!gOn[j]) continue;
+#pragma unroll
+      for (int p = 0; p < BS; ++p)
+#pragma unroll
+        for (int q = 0; q < BS; ++q)
+          gout[gM[j] * L::E2 + (gI[j] * BS + p) * KP + gJ[j] * BS + q] = gacc[j][p * BS + q];
     }
   } else {
-    float* gred = xn_t;  // GROUPS * E2 * 2 floats = NT * W * 2 <= 3 * R * KP
+    // groups -> one sum per entry, group order fixed
+    float* gred = xn_t;  // ACTIVE * BS^2 floats
+    if (gact) {
 #pragma unroll
-    for (int w = 0; w < L::W; ++w) {
-      gred[(grp * L::E2 + eown + w) * 2 + 0] = accA[w];
-      gred[(grp * L::E2 + eown + w) * 2 + 1] = accB[w];
+      for (int q = 0; q < BS * BS; ++q) gred[(ggrp * G::TASKS + gT[0]) * BS * BS + q] = gacc[0][q];
     }
     __syncthreads();
-    if (grp == 0) {
-#pragma unroll
-      for (int w = 0; w < L::W; ++w) {
-        float sa = 0.f, sb = 0.f;
-        for (int g = 0; g < L::GROUPS; ++g) {
-          sa += gred[(g * L::E2 + eown + w) * 2 + 0];
-          sb += gred[(g * L::E2 + eown + w) * 2 + 1];
-        }
-        gout[eown + w] = sa;
-        if constexpr (!EVAL) gout[L::E2 + eown + w] = sb;
-      }
+    for (int e = tid; e < G::TASKS * BS * BS; e += L::NT) {
+      float sum = 0.f;
+#pragma unroll 1
+      for (int g = 0; g < G::GROUPS; ++g) sum += gred[g * G::TASKS * BS * BS + e];
+      int m, I, J;
+      gram_task(e / (BS * BS), G::NBLK, G::NB1, m, I, J);
+      const int p = (e % (BS * BS)) / BS, q = e % BS;
+      gout[m * L::E2 + (I * BS + p) * KP + J * BS + q] = sum;
     }
   }
 }
 
 // Partial products of chunked (very high degree) rows: hv_part[c] = sum over
 // chunk c's nonzeros of s_ij * xbar_j.  Teams stride over chunks in rounds so
-// that the gather stays warp-uniform.
-template <int KP, bool MIXED>
+// that the gather stays warp-uniform.  EVAL: for an objective-only pass over
+// buffer eval_sel (float32 iterate and values).
+template <int KP, bool MIXED, bool EVAL>
 __global__ void __launch_bounds__(Lay<KP>::NT) heavy_kernel(PassArgs a) {
   using L = Lay<KP>;
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  int64_t pass;
+  if constexpr (!EVAL) {
+    volatile FistaState* vs = a.st;
+    if (vs->done || vs->pass >= vs->limit) return;
+    pass = vs->pass;
+  } else {
+    pass = a.eval_sel;
+  }
   const float* P = (pass & 1) ? a.X1 : a.X0;
   const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -531,27 +578,25 @@ __global__ void __launch_bounds__(Lay<KP>::NT) heavy_kernel(PassArgs a) {
 
 struct FoldArgs {
   FistaState* st;
-  const float* gram_part;   // [parts][2][KP][KP]
+  const float* gram_part;   // [parts][2][KP][KP], upper BS x BS blocks written
   const double* sc_part;    // [parts][4]
   int32_t parts;
-  int32_t eval;             // 1: objective-only pass (A only)
-  int32_t eval_init;        // 1: also seed the solver (A_0, Gy, gram2_cur)
+  int32_t eval;             // 1: objective-only pass (Gram of the evaluated iterate only)
+  int32_t eval_init;        // 1: also seed the solver (G(Y^1) = Gram of Xbar^0, gram2_cur)
   int32_t pad_;
-  double* A0;               // Gram of Xbar^j in A_{j&1}, KP x KP float64
-  double* A1;
-  double* B;                // Xbar^{pass}^T Xbar^{pass-1}
-  double* Aeval;            // objective-only result
+  double* A;                // KP x KP float64: Gram of the newest iterate (scratch)
+  double* G;                // KP x KP float64: Gram of the next extrapolated point (scratch)
   float* Gy;                // KP x KP float32 for the next pass
 };
 
 // Sums the per-block partials in block order (float64), evaluates the loss of
-// Xbar^{n-1}, applies the stop rule, advances t and the momentum factor, and
-// forms G(Y^{n+1}) = (1+b)^2 A_n - b(1+b)(B_n + B_n^T) + b^2 A_{n-1} minus its
-// mean entry (the mean shift leaves the projection unchanged because rows of
-// Y sum to one: P(v + c 1) = P(v)).
+// Xbar^{n-1}, applies the stop rule, advances t and the momentum factors, and
+// stores G(Y^{n+1}) minus its mean entry in float32 (the mean shift leaves the
+// projection unchanged because rows of Y sum to one: P(v + c 1) = P(v)).
 template <int KP>
 __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   constexpr int E2 = KP * KP;
+  constexpr int BS = KP < 4 ? KP : 4;
   FistaState* st = f.st;
   volatile FistaState* vs = st;
   if (!f.eval && (vs->done || vs->pass >= vs->limit)) return;
@@ -559,13 +604,13 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   const int64_t nnew = pass + 1;
   const int tid = threadIdx.x;
   const int nent = f.eval ? E2 : 2 * E2;
-  double* Adst = f.eval ? f.Aeval : ((nnew & 1) ? f.A1 : f.A0);
   const int e = blockIdx.x * 256 + tid;
   if (e < nent) {
+    const int m = e / E2, r = (e % E2) / KP, c = e % KP;
+    const int src = m * E2 + ((r / BS <= c / BS) ? r * KP + c : c * KP + r);
     double s = 0.0;
-    for (int c = 0; c < f.parts; ++c) s += (double)f.gram_part[(size_t)c * 2 * E2 + e];
-    if (e < E2) Adst[e] = s;
-    else f.B[e - E2] = s;
+    for (int p = 0; p < f.parts; ++p) s += (double)f.gram_part[(size_t)p * 2 * E2 + src];
+    (m == 0 ? f.A : f.G)[r * KP + c] = s;
   }
   __threadfence();
   __syncthreads();
@@ -576,12 +621,11 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   __threadfence();
 
   __shared__ double red[256];
-  __shared__ double sc[4];
   const int k = st->k;
-  // ||A_new||_F^2 (fixed-order tree)
+  // ||A||_F^2 (fixed-order tree)
   double part = 0.0;
   for (int i = tid; i < E2; i += 256) {
-    const double v = __ldcg(Adst + i);
+    const double v = __ldcg(f.A + i);
     part += v * v;
   }
   red[tid] = part;
@@ -599,15 +643,11 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
       pg += __ldcg(f.sc_part + c * 4 + 1);
       bad += __ldcg(f.sc_part + c * 4 + 2);
     }
-    double beta_next = 0.0;
     if (f.eval) {
       st->eval_trace = tr;
       st->eval_gram2 = gram2_new;
       st->eval_f = st->S2 - 2.0 * tr + gram2_new;
-      if (f.eval_init) {
-        st->gram2_cur = gram2_new;
-        st->beta = 0.0;
-      }
+      if (f.eval_init) st->gram2_cur = gram2_new;
     } else {
       // loss of Xbar^{pass} (= Xbar^{n-1} for this pass n = pass + 1)
       const double loss = st->S2 - 2.0 * tr + st->gram2_cur;
@@ -640,37 +680,27 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
       }
       st->loss_prev = loss;
       st->gram2_cur = gram2_new;
-      const double t = st->t;
-      const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      beta_next = st->accel ? (t - 1.0) / t_next : 0.0;
-      st->t = t_next;
-      st->beta = beta_next;
+      // t_{n+1}, t_{n+2} and the momentum factors of the next two passes
+      const double t0 = st->t;
+      const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t0 * t0));
+      const double t2 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t1 * t1));
+      st->t = t1;
+      st->beta = st->accel ? (t0 - 1.0) / t1 : 0.0;
+      st->beta_next = st->accel ? (t1 - 1.0) / t2 : 0.0;
       st->out_iter = out;
       st->status = status;
       st->done = done;
       st->pass = nnew;
     }
-    sc[3] = beta_next;
   }
   __syncthreads();
-  // G(Y) for the next pass, then subtract its mean over the k x k block
+  // float32 G(Y) for the next pass, minus its mean over the k x k block
   if (!f.eval || f.eval_init) {
-    const double b = sc[3];
-    const double* An = f.eval ? f.Aeval : Adst;
-    const double* Ao = f.eval ? f.Aeval : ((nnew & 1) ? f.A0 : f.A1);
+    const double* Gsrc = f.eval ? f.A : f.G;
     double msum = 0.0;
     for (int i = tid; i < E2; i += 256) {
       const int r = i / KP, c = i % KP;
-      if (r < k && c < k) {
-        double g;
-        if (f.eval) {
-          g = __ldcg(An + i);
-        } else {
-          const double bb = __ldcg(f.B + i) + __ldcg(f.B + c * KP + r);
-          g = (1.0 + b) * (1.0 + b) * __ldcg(An + i) - b * (1.0 + b) * bb + b * b * __ldcg(Ao + i);
-        }
-        msum += g;
-      }
+      if (r < k && c < k) msum += __ldcg(Gsrc + i);
     }
     red[tid] = msum;
     __syncthreads();
@@ -681,18 +711,7 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
     const double mean = red[0] / ((double)k * (double)k);
     for (int i = tid; i < E2; i += 256) {
       const int r = i / KP, c = i % KP;
-      double g = 0.0;
-      if (r < k && c < k) {
-        if (f.eval) {
-          g = __ldcg(An + i);
-        } else {
-          const double bb = __ldcg(f.B + i) + __ldcg(f.B + c * KP + r);
-          g = (1.0 + b) * (1.0 + b) * __ldcg(An + i) - b * (1.0 + b) * bb + b * b * __ldcg(Ao + i);
-        }
-        g -= mean;
-      }
-      f.Gy[i] = (float)g;
-      if (f.eval && f.eval_init) f.A0[i] = __ldcg(An + i);
+      f.Gy[i] = (r < k && c < k) ? (float)(__ldcg(Gsrc + i) - mean) : 0.0f;
     }
     if (tid == 0) st->shift = mean;
   }

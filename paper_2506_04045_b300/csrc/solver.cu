@@ -83,9 +83,10 @@ struct KPOps {
   static void launch_eval(const PassArgs& a, int grid, cudaStream_t s) {
     fista_pass_kernel<KP, false, true><<<grid, L::NT, pass_smem_bytes<KP>(true), s>>>(a);
   }
-  static void launch_heavy(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-    if (mixed) heavy_kernel<KP, true><<<grid, L::NT, 0, s>>>(a);
-    else heavy_kernel<KP, false><<<grid, L::NT, 0, s>>>(a);
+  static void launch_heavy(const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s) {
+    if (eval) heavy_kernel<KP, false, true><<<grid, L::NT, 0, s>>>(a);
+    else if (mixed) heavy_kernel<KP, true, false><<<grid, L::NT, 0, s>>>(a);
+    else heavy_kernel<KP, false, false><<<grid, L::NT, 0, s>>>(a);
   }
   static void launch_fold(const FoldArgs& f, cudaStream_t s) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
@@ -125,8 +126,8 @@ static void kp_launch_pass(int KP, const PassArgs& a, int grid, bool mixed, cuda
 static void kp_launch_eval(int KP, const PassArgs& a, int grid, cudaStream_t s) {
   FC_DISPATCH(KP, Ops::launch_eval(a, grid, s));
 }
-static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, s));
+static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
 
@@ -176,7 +177,7 @@ static void ctx_free(cluster_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
-                  c->A[1], c->B, c->Aeval, c->Gy, c->gram_part, c->sc_part, c->st};
+                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -190,7 +191,7 @@ static PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
   a.val = (c->mixed && !eval_exact) ? (const void*)c->val16 : (const void*)c->val;
   a.order = c->order;
   a.cta_pos = c->cta_pos;
-  a.n_heavy = eval_exact ? 0 : c->n_heavy;
+  a.n_heavy = c->n_heavy;
   a.chunk_ptr = c->chunk_ptr;
   a.chunk_e0 = c->chunk_e0;
   a.chunk_e1 = c->chunk_e1;
@@ -220,10 +221,8 @@ static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
   f.parts = c->parts;
   f.eval = eval;
   f.eval_init = eval_init;
-  f.A0 = c->A[0];
-  f.A1 = c->A[1];
-  f.B = c->B;
-  f.Aeval = c->Aeval;
+  f.A = c->A[0];
+  f.G = c->A[1];
   f.Gy = c->Gy;
   return f;
 }
@@ -231,7 +230,7 @@ static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
 // Enqueue one iteration (heavy chunks, fused pass, fold).
 static void enqueue_pass(const cluster_ctx* c, cudaStream_t s) {
   PassArgs a = make_pass_args(c, false);
-  if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, s);
+  if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
   kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
   kp_launch_fold(c->KP, make_fold_args(c, 0, 0), s);
 }
@@ -240,6 +239,7 @@ static void enqueue_pass(const cluster_ctx* c, cudaStream_t s) {
 static void enqueue_eval(const cluster_ctx* c, int sel, int init, cudaStream_t s) {
   PassArgs a = make_pass_args(c, true);
   a.eval_sel = sel;
+  if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, false, true, s);
   kp_launch_eval(c->KP, a, c->parts, s);
   kp_launch_fold(c->KP, make_fold_args(c, 1, init), s);
 }
@@ -566,11 +566,7 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   const size_t e2 = (size_t)c->KP * c->KP;
   FC_CUDA(cudaMalloc(&c->A[0], sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->A[1], sizeof(double) * e2));
-  FC_CUDA(cudaMalloc(&c->B, sizeof(double) * e2));
-  FC_CUDA(cudaMalloc(&c->Aeval, sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->Gy, sizeof(float) * e2));
-  FC_CUDA(cudaMemsetAsync(c->A[1], 0, sizeof(double) * e2, s));
-  FC_CUDA(cudaMemsetAsync(c->B, 0, sizeof(double) * e2, s));
   FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * c->parts));
   FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * c->parts));
   FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
@@ -584,7 +580,8 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   h.L = L;
   h.tol = opt.tol;
   h.t = 1.0;
-  h.beta = 0.0;
+  h.beta = 0.0;       // beta_1 = 0 (X^1 = Xbar^0)
+  h.beta_next = 0.0;  // beta_2 = (t_1 - 1) / t_2 = 0
   h.max_iter = opt.max_iter;
   h.f_iter = -1;
   h.out_iter = 0;
@@ -627,7 +624,7 @@ static cluster_status finalize_loss(cluster_ctx* c) {
   return CLUSTER_OK;
 }
 
-// checkpoint layout: header, FistaState, A0, A1, B (float64 KP^2 each), Gy, X0, X1, Zp [, XS0, XS1]
+// checkpoint layout: header, FistaState, Gy (float32 KP^2), X0, X1, Zp [, XS0, XS1]
 struct StateHeader {
   uint64_t magic;
   int64_t n;
@@ -637,10 +634,54 @@ static const uint64_t kStateMagic = 0x46434C5553543031ull;  // "FCLUST01"
 
 static size_t state_bytes(const cluster_ctx* c) {
   const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
-  size_t b = sizeof(StateHeader) + sizeof(FistaState) + 3 * e2 * sizeof(double) + e2 * sizeof(float) +
-             3 * nk * sizeof(float);
+  size_t b = sizeof(StateHeader) + sizeof(FistaState) + e2 * sizeof(float) + 3 * nk * sizeof(float);
   if (c->mixed) b += 2 * nk * sizeof(__nv_bfloat16);
   return b;
+}
+
+// Objective-only evaluation with a temporary context: the same degree
+// schedule and chunked rows as a solver, so power-law hubs stay balanced.
+static cluster_status objective_impl(const cluster_csr* S, int32_t k, const float* U, void* stream, double* f,
+                                     cluster_ctx* c) {
+  c->stream = (cudaStream_t)stream;
+  c->n = S->n;
+  c->nnz = S->nnz;
+  c->k = k;
+  c->KP = padded_k(k);
+  c->mixed = false;
+  FC_CUDA(cudaGetDevice(&c->dev));
+  cudaStream_t s = c->stream;
+  FC_TRY(prepare_rowptr(S, s, &c->rp, &c->rp_owned));
+  c->col = S->col;
+  c->val = S->val;
+  FC_CUDA(kp_setup_attrs(c->KP));
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int occ = kp_occupancy(c->KP, false);
+  const int R = kp_rows_per_tile(c->KP);
+  int64_t parts = (int64_t)sms * occ;
+  if (parts > (c->n + R - 1) / R) parts = (c->n + R - 1) / R;
+  c->parts = (int)std::max<int64_t>(1, parts);
+  c->heavy_grid = sms * occ;
+  c->heavy_H = std::max<int64_t>(64, 16384 / c->KP);
+  FC_TRY(build_schedule(c));
+  const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
+  FC_CUDA(cudaMalloc(&c->X[0], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->A[0], sizeof(double) * e2));
+  FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * c->parts));
+  FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * c->parts));
+  FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
+  FistaState h;
+  memset(&h, 0, sizeof(h));
+  h.k = k;
+  FC_TRY(sum_squares(S->val, S->nnz, s, &h.S2));
+  FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U, c->n, k, c->KP, c->X[0], nullptr, nullptr, nullptr);
+  enqueue_eval(c, 0, 0, s);
+  FC_CUDA(cudaGetLastError());
+  FC_TRY(read_state(c));
+  *f = c->host_st.eval_f;
+  return CLUSTER_OK;
 }
 
 }  // namespace fc
@@ -715,7 +756,7 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
   for (int64_t i = 0; i < iters; ++i) {
     cudaEvent_t* e = &ev[(size_t)(4 * i)];
     cudaEventRecord(e[0], s);
-    if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, s);
+    if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
     cudaEventRecord(e[1], s);
     kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
     cudaEventRecord(e[2], s);
@@ -812,10 +853,9 @@ extern "C" cluster_status cluster_get_state(cluster_ctx* c, void* buf, size_t by
   struct Seg {
     const void* src;
     size_t b;
-  } segs[] = {{c->st, sizeof(FistaState)}, {c->A[0], e2 * 8}, {c->A[1], e2 * 8}, {c->B, e2 * 8},
-              {c->Gy, e2 * 4},           {c->X[0], nk * 4}, {c->X[1], nk * 4}, {c->Zp, nk * 4},
-              {c->XS[0], nk * 2},        {c->XS[1], nk * 2}};
-  const int nseg = c->mixed ? 10 : 8;
+  } segs[] = {{c->st, sizeof(FistaState)}, {c->Gy, e2 * 4},   {c->X[0], nk * 4},
+              {c->X[1], nk * 4},          {c->Zp, nk * 4},   {c->XS[0], nk * 2}, {c->XS[1], nk * 2}};
+  const int nseg = c->mixed ? 7 : 5;
   for (int i = 0; i < nseg; ++i) {
     FC_CUDA(cudaMemcpyAsync(p, segs[i].src, segs[i].b, cudaMemcpyDeviceToHost, c->stream));
     p += segs[i].b;
@@ -842,10 +882,9 @@ extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, siz
   struct Seg {
     void* dst;
     size_t b;
-  } segs[] = {{c->st, sizeof(FistaState)}, {c->A[0], e2 * 8}, {c->A[1], e2 * 8}, {c->B, e2 * 8},
-              {c->Gy, e2 * 4},           {c->X[0], nk * 4}, {c->X[1], nk * 4}, {c->Zp, nk * 4},
-              {c->XS[0], nk * 2},        {c->XS[1], nk * 2}};
-  const int nseg = c->mixed ? 10 : 8;
+  } segs[] = {{c->st, sizeof(FistaState)}, {c->Gy, e2 * 4},   {c->X[0], nk * 4},
+              {c->X[1], nk * 4},          {c->Zp, nk * 4},   {c->XS[0], nk * 2}, {c->XS[1], nk * 2}};
+  const int nseg = c->mixed ? 7 : 5;
   for (int i = 0; i < nseg; ++i) {
     const void* src = (i == 0) ? (const void*)&fs : (const void*)p;
     FC_CUDA(cudaMemcpyAsync(segs[i].dst, src, segs[i].b, cudaMemcpyHostToDevice, c->stream));
@@ -871,58 +910,13 @@ extern "C" cluster_status cluster_objective(const cluster_csr* S, int32_t k, con
   clear_error();
   FC_TRY(check_csr_args(S, k));
   if (!U || !f) FC_EINVAL("NULL argument");
-  cudaStream_t s = (cudaStream_t)stream;
-  const int64_t n = S->n, nnz = S->nnz;
-  cluster_ctx tmp;  // only the fields the objective pass reads
-  tmp.stream = s;
-  tmp.n = n;
-  tmp.k = k;
-  tmp.KP = padded_k(k);
-  tmp.mixed = false;
-  const int KP = tmp.KP;
-  int dev = 0;
-  FC_CUDA(cudaGetDevice(&dev));
-  FC_CUDA(kp_setup_attrs(KP));
-  int sms = 0;
-  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int R = kp_rows_per_tile(KP);
-  int64_t parts = (int64_t)sms * 2;
-  if (parts > (n + R - 1) / R) parts = (n + R - 1) / R;
-  if (parts < 1) parts = 1;
-  tmp.parts = (int)parts;
-  const size_t e2 = (size_t)KP * KP, nk = (size_t)n * KP;
-  int64_t* rp_owned = nullptr;
-  FC_TRY(prepare_rowptr(S, s, &tmp.rp, &rp_owned));
-  tmp.col = S->col;
-  tmp.val = S->val;
-  cluster_status st = CLUSTER_OK;
-  cudaError_t e = cudaSuccess;
-  do {
-    if ((e = cudaMalloc(&tmp.X[0], sizeof(float) * nk)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&tmp.Aeval, sizeof(double) * e2)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&tmp.gram_part, sizeof(float) * 2 * e2 * parts)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&tmp.sc_part, sizeof(double) * 4 * parts)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&tmp.st, sizeof(FistaState))) != cudaSuccess) break;
-    FistaState h;
-    memset(&h, 0, sizeof(h));
-    h.k = k;
-    st = sum_squares(S->val, nnz, s, &h.S2);
-    if (st != CLUSTER_OK) break;
-    cudaMemcpyAsync(tmp.st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
-    pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U, n, k, KP, tmp.X[0], nullptr, nullptr, nullptr);
-    enqueue_eval(&tmp, 0, 0, s);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    FistaState out;
-    cudaMemcpyAsync(&out, tmp.st, sizeof(out), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-    *f = out.eval_f;
-  } while (0);
-  if (e != cudaSuccess) {
-    set_error("cluster_objective: %s", cudaGetErrorString(e));
-    st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+  cluster_ctx* c = new (std::nothrow) cluster_ctx();
+  if (!c) {
+    set_error("out of host memory");
+    return CLUSTER_ENOMEM;
   }
-  void* bufs[] = {rp_owned, tmp.X[0], tmp.Aeval, tmp.gram_part, tmp.sc_part, tmp.st};
-  for (void* p : bufs)
-    if (p) cudaFree(p);
+  cluster_status st = objective_impl(S, k, U, stream, f, c);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  ctx_free(c);
   return st;
 }

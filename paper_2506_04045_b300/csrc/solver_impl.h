@@ -40,10 +40,8 @@ struct cluster_ctx {
   float* X[2] = {nullptr, nullptr};
   __nv_bfloat16* XS[2] = {nullptr, nullptr};
   float* Zp = nullptr;
-  double* A[2] = {nullptr, nullptr};
-  double* B = nullptr;
-  double* Aeval = nullptr;
-  float* Gy = nullptr;
+  double* A[2] = {nullptr, nullptr};  // float64 fold scratch: Gram of Xbar^n, Gram of Y^{n+1}
+  float* Gy = nullptr;                 // float32 G(Y) (minus its mean) read by the next pass
   float* gram_part = nullptr;
   double* sc_part = nullptr;
   fc::FistaState* st = nullptr;

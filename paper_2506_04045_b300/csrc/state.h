@@ -18,6 +18,7 @@ struct FistaState {
   double tol;         // stopping tolerance
   double t;           // t_n of the pass about to run (t_1 = 1)
   double beta;        // momentum factor (t_{n-1} - 1) / t_n of the pass about to run
+  double beta_next;   // momentum factor of the pass after it (forms Y^{n+1} one pass early)
   double gram2_cur;   // ||Xbar^{pass}^T Xbar^{pass}||_F^2
   double loss_prev;   // newest known loss before loss_last (stop test)
   double loss_last;   // f(Xbar^{f_iter})
