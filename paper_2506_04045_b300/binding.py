@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libcluster.so")
+# CLUSTER_LIB_PATH selects another build of the same library (tuning variants)
+_LIB_PATH = os.environ.get("CLUSTER_LIB_PATH") or os.path.join(_HERE, "libcluster.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -98,7 +99,7 @@ def load() -> ctypes.CDLL:
         if _lib is not None:
             return _lib
         from . import build as _build
-        if not _build.up_to_date():
+        if _LIB_PATH == _build.LIB and not _build.up_to_date():
             try:
                 _build.build()
             except Exception as exc:  # no nvcc, or a compile error

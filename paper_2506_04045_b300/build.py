@@ -35,16 +35,20 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Compile every CUDA/C++ source of the library into one shared object."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, out: str | None = None,
+          defines: tuple = ()) -> str:
+    """Compile every CUDA/C++ source of the library into one shared object.
+    ``out``/``defines`` build a variant (e.g. ``("FC_MINB32=3",)``) elsewhere."""
+    target = out or LIB
+    if out is None and not defines and not force and up_to_date():
         return LIB
     cmd = [_nvcc(), "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", *ARCH, "-I", os.path.join(ROOT, "include")]
     if ptxas_v:
         cmd += ["-Xptxas", "-v"]
+    cmd += [f"-D{d}" for d in defines]
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
-    cmd += ["-o", LIB + ".tmp", "-lcudart"]
+    cmd += ["-o", target + ".tmp", "-lcudart"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -52,10 +56,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
     if ptxas_v or verbose:
         sys.stderr.write(res.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(target + ".tmp", target)
+    return target
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv)
-    print(LIB)
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--ptxas-v", action="store_true")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("-D", dest="defines", action="append", default=[])
+    a = ap.parse_args()
+    print(build(force=a.force, verbose=True, ptxas_v=a.ptxas_v, out=a.out, defines=tuple(a.defines)))

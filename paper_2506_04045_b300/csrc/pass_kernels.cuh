@@ -41,6 +41,10 @@ namespace fc {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+#ifndef FC_MINB32
+#define FC_MINB32 4  // resident 256-thread blocks per SM the k <= 32 pass is sized for
+#endif
+
 template <int KP>
 struct Lay {
   static constexpr int VEC = KP < 4 ? KP : 4;      // features per lane
@@ -53,7 +57,7 @@ struct Lay {
   static constexpr int PER = NB / T;                // (col, val) pairs each lane fetches per batch
   static constexpr int E2 = KP * KP;
   // resident blocks per SM the register budget is sized for
-  static constexpr int MINB = KP <= 4 ? 2 : (KP == 8 ? 3 : (KP <= 32 ? 4 : (KP == 64 ? 2 : 1)));
+  static constexpr int MINB = KP <= 4 ? 2 : (KP == 8 ? 3 : (KP == 16 ? 4 : (KP == 32 ? FC_MINB32 : (KP == 64 ? 2 : 1))));
 };
 
 // Symmetric Gram accumulation: the KP x KP matrix is cut into BS x BS blocks
@@ -208,7 +212,9 @@ __device__ __forceinline__ float team_sum(float v) {
 }
 
 // acc += sum_{e in [lo, hi)} val[e] * Xg[col[e], f0 .. f0+VEC).  `batches` must
-// be the same on every lane of the warp (the maximum over its teams).
+// be the same on every lane of the warp (the maximum over its teams).  The
+// (col, val) pairs of batch j+1 are fetched while the gathers of batch j are in
+// flight, so a batch costs one memory round trip.
 template <int KP, bool MIXED>
 __device__ __forceinline__ void gather(const int32_t* __restrict__ col, const void* __restrict__ valp,
                                        const void* __restrict__ Xg, int64_t lo, int64_t hi, int batches,
@@ -216,28 +222,42 @@ __device__ __forceinline__ void gather(const int32_t* __restrict__ col, const vo
   using L = Lay<KP>;
   using VT = typename GatherT<MIXED>::V;
   const VT* val = reinterpret_cast<const VT*>(valp);
-  for (int j = 0; j < batches; ++j) {
-    const int64_t e0 = lo + (int64_t)j * L::NB;
-    int ci[L::PER];
-    float cv[L::PER];
+  int ci[L::PER];
+  float cv[L::PER];
 #pragma unroll
-    for (int p = 0; p < L::PER; ++p) {
-      const int64_t e = e0 + lt + p * L::T;
-      const bool ok = e < hi;
-      ci[p] = ok ? __ldg(col + e) : 0;
-      cv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
-    }
+  for (int p = 0; p < L::PER; ++p) {
+    const int64_t e = lo + lt + p * L::T;
+    const bool ok = batches > 0 && e < hi;
+    ci[p] = ok ? __ldg(col + e) : 0;
+    cv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
+  }
+  for (int j = 0; j < batches; ++j) {
     float xv[L::NB][L::VEC];
 #pragma unroll
     for (int u = 0; u < L::NB; ++u) {
       const int c = L::T > 1 ? __shfl_sync(kFull, ci[u / L::T], u % L::T, L::T) : ci[u];
       load_feat<L::VEC, MIXED>(Xg, (int64_t)c * KP + f0, xv[u]);
     }
+    int ni[L::PER];
+    float nv[L::PER];
+    const int64_t e1 = lo + (int64_t)(j + 1) * L::NB;
+#pragma unroll
+    for (int p = 0; p < L::PER; ++p) {
+      const int64_t e = e1 + lt + p * L::T;
+      const bool ok = e < hi;
+      ni[p] = ok ? __ldg(col + e) : 0;
+      nv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
+    }
 #pragma unroll
     for (int u = 0; u < L::NB; ++u) {
       const float v = L::T > 1 ? __shfl_sync(kFull, cv[u / L::T], u % L::T, L::T) : cv[u];
 #pragma unroll
       for (int q = 0; q < L::VEC; ++q) acc[q] = fmaf(v, xv[u][q], acc[q]);
+    }
+#pragma unroll
+    for (int p = 0; p < L::PER; ++p) {
+      ci[p] = ni[p];
+      cv[p] = nv[p];
     }
   }
 }
@@ -295,19 +315,15 @@ __host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
   return sizeof(float) * ((eval ? 0 : (size_t)L::E2) + (tiles > red ? tiles : red)) + 64;
 }
 
-// One pass.  EVAL: objective-only (z = S X, p_i, Gram of X; no update).
+// One block's share of a pass: positions [p0, p1) of the row order, partial
+// results into slot `slot` of gram_part / sc_part.  `pass` is the index of the
+// newest iterate (the buffer parity), or the evaluated buffer when EVAL.
+// EVAL: objective-only (z = S X, p_i, Gram of X; no update).
 template <int KP, bool MIXED, bool EVAL>
-__global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(PassArgs a) {
+__device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int64_t p0, int64_t p1, int slot,
+                                           float* smem) {
   using L = Lay<KP>;
   FistaState* st = a.st;
-  int64_t pass;
-  if constexpr (!EVAL) {
-    volatile FistaState* vs = st;
-    if (vs->done || vs->pass >= vs->limit) return;
-    pass = vs->pass;
-  } else {
-    pass = a.eval_sel;
-  }
   const float beta = EVAL ? 0.f : (float)st->beta;
   const float beta_next = EVAL ? 0.f : (float)st->beta_next;
   const float tau4 = EVAL ? 0.f : (float)(4.0 * st->tau);
@@ -316,7 +332,6 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
   const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
   __nv_bfloat16* XSo = (pass & 1) ? a.XS0 : a.XS1;
 
-  extern __shared__ __align__(16) float smem[];
   float* Gs = smem;
   float* xn_t = Gs + (EVAL ? 0 : L::E2);
   float* yn_t = xn_t + L::R * KP;
@@ -357,19 +372,15 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
   double tr_acc = 0.0, pg_acc = 0.0;
   int bad = 0;
 
-  int64_t p0, p1;
-  if (a.cta_pos) {
-    p0 = a.cta_pos[blockIdx.x];
-    p1 = a.cta_pos[blockIdx.x + 1];
-  } else {
-    p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
-    p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-  }
-
+  int64_t next_row = (p0 + team < p1) ? (a.order ? (int64_t)a.order[p0 + team] : p0 + team) : 0;
   for (int64_t base = p0; base < p1; base += L::R) {
     const int64_t pos = base + team;
     const bool active = pos < p1;
-    const int64_t row = active ? (a.order ? (int64_t)a.order[pos] : pos) : 0;
+    const int64_t row = active ? next_row : 0;
+    {  // row id of the next tile, fetched one tile ahead
+      const int64_t np = pos + L::R;
+      next_row = (np < p1) ? (a.order ? (int64_t)a.order[np] : np) : 0;
+    }
     float acc[L::VEC];
 #pragma unroll
     for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
@@ -388,12 +399,18 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
       lo = a.row_ptr[row];
       hi = a.row_ptr[row + 1];
     }
+    // own-row loads are independent of the gather: issue them first
+    float pv[L::VEC];
+    load_row<L::VEC>(P + row * KP + f0, pv);
+    float qv[L::VEC], zp[L::VEC];
+    if constexpr (!EVAL) {
+      load_row<L::VEC>(Q + row * KP + f0, qv);
+      load_row<L::VEC>(a.Zp + row * KP + f0, zp);
+    }
     const int nb = (int)((hi - lo + L::NB - 1) / L::NB);
     const int batches = __reduce_max_sync(kFull, nb);
     gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
 
-    float pv[L::VEC];
-    load_row<L::VEC>(P + row * KP + f0, pv);
     float d = 0.f;
 #pragma unroll
     for (int q = 0; q < L::VEC; ++q) d = fmaf(pv[q], acc[q], d);
@@ -401,9 +418,7 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
     if (active && lt == 0) tr_acc += (double)d;
 
     if constexpr (!EVAL) {
-      float qv[L::VEC], zp[L::VEC], y[L::VEC], sy[L::VEC];
-      load_row<L::VEC>(Q + row * KP + f0, qv);
-      load_row<L::VEC>(a.Zp + row * KP + f0, zp);
+      float y[L::VEC], sy[L::VEC];
 #pragma unroll
       for (int q = 0; q < L::VEC; ++q) {
         y[q] = fmaf(beta, pv[q] - qv[q], pv[q]);
@@ -503,13 +518,13 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
       p += dred[w * 3 + 1];
       b += dred[w * 3 + 2];
     }
-    a.sc_part[blockIdx.x * 4 + 0] = t;
-    a.sc_part[blockIdx.x * 4 + 1] = p;
-    a.sc_part[blockIdx.x * 4 + 2] = b;
-    a.sc_part[blockIdx.x * 4 + 3] = 0.0;
+    a.sc_part[slot * 4 + 0] = t;
+    a.sc_part[slot * 4 + 1] = p;
+    a.sc_part[slot * 4 + 2] = b;
+    a.sc_part[slot * 4 + 3] = 0.0;
   }
   __syncthreads();
-  float* gout = a.gram_part + (size_t)blockIdx.x * 2 * L::E2;
+  float* gout = a.gram_part + (size_t)slot * 2 * L::E2;
   if constexpr (G::GROUPS == 1) {
 #pragma unroll
     for (int j = 0; j < G::TPT; ++j) {
@@ -538,6 +553,30 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
       gout[m * L::E2 + (I * BS + p) * KP + J * BS + q] = sum;
     }
   }
+}
+
+// One pass of one instance: block b takes positions [cta_pos[b], cta_pos[b+1])
+// (an even split when cta_pos is null) and partial slot b.
+template <int KP, bool MIXED, bool EVAL>
+__global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(PassArgs a) {
+  int64_t pass;
+  if constexpr (!EVAL) {
+    volatile FistaState* vs = a.st;
+    if (vs->done || vs->pass >= vs->limit) return;
+    pass = vs->pass;
+  } else {
+    pass = a.eval_sel;
+  }
+  int64_t p0, p1;
+  if (a.cta_pos) {
+    p0 = a.cta_pos[blockIdx.x];
+    p1 = a.cta_pos[blockIdx.x + 1];
+  } else {
+    p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
+    p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  }
+  extern __shared__ __align__(16) float smem[];
+  pass_range<KP, MIXED, EVAL>(a, pass, p0, p1, blockIdx.x, smem);
 }
 
 // Partial products of chunked (very high degree) rows: hv_part[c] = sum over
