@@ -206,6 +206,28 @@ CLUSTER_API cluster_status cluster_get_U(cluster_ctx* ctx, float* U_out);
 CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, const float* U,
                                              void* stream, double* f);
 
+/* The objective f(U) like cluster_objective, but without allocating any
+ * memory.  The paper has no counterpart: this entry point is for callers that
+ * must not call cudaMalloc at the point where they evaluate f — for instance a
+ * service that gives all free device memory to its own pool at start-up, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device.  Its device scratch is one fixed array of about 2.7 MB compiled into
+ * the library, which every GPU that loads the library keeps until the process
+ * exits.
+ * Limits (EINVAL otherwise): k in {2, 4, 8, 16, 32} (U, n x k device, is read
+ * in place, 16-byte aligned; 8-byte for k = 2), S with int64 row pointers
+ * (index64 = 1), n < 2^31.  Rows are split evenly over the GPU rather than
+ * ordered by degree, so graphs with rows of very high degree run slower than
+ * with cluster_objective.
+ * The first call on a device looks up the scratch array's device address for
+ * that device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and each call resets what must
+ * start at zero, so calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller.  The call synchronises
+ * `stream` and writes the value to *f. */
+CLUSTER_API cluster_status cluster_objective_static(const cluster_csr* S, int32_t k, const float* U,
+                                                    void* stream, double* f);
+
 /* Checkpoint.  The state is everything a resumed run needs to continue bit
  * for bit: the two newest iterates, the stored product S*Xbar^{n-1}, the
  * float64 Gram matrices and scalars.  cluster_state_size gives the byte size;

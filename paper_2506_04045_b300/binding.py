@@ -78,6 +78,8 @@ _SIGS = {
     "cluster_get_U": (ctypes.c_int, [_P, _P]),
     "cluster_objective": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.c_int32, _P, _P,
                                          ctypes.POINTER(ctypes.c_double)]),
+    "cluster_objective_static": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.c_int32, _P, _P,
+                                                ctypes.POINTER(ctypes.c_double)]),
     "cluster_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "cluster_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
@@ -247,6 +249,16 @@ def objective(row_ptr, col, val, U, stream=None) -> float:
     csr = make_csr(row_ptr, col, val)
     f = ctypes.c_double()
     check(lib.cluster_objective(ctypes.byref(csr), int(U.shape[1]), _ptr(U), _stream_ptr(stream), ctypes.byref(f)))
+    return f.value
+
+
+def objective_static(row_ptr, col, val, U, stream=None) -> float:
+    """f(U) through cluster_objective_static (no device allocation; device tensors)."""
+    lib = load()
+    csr = make_csr(row_ptr, col, val)
+    f = ctypes.c_double()
+    check(lib.cluster_objective_static(ctypes.byref(csr), int(U.shape[1]), _ptr(U), _stream_ptr(stream),
+                                       ctypes.byref(f)))
     return f.value
 
 
