@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--forms", default="fp32,mixed")
     p.add_argument("--cpu-sample-n", type=int, default=1_000_000)
     p.add_argument("--cpu-iters", type=int, default=2)
+    p.add_argument("--fused", action="store_true", help="one fused kernel per iteration instead of the split form")
     return p.parse_args()
 
 
@@ -127,19 +128,26 @@ class ClockSampler:
 # algorithmic bytes (per iteration) of the fused pass
 # ---------------------------------------------------------------------------
 def alg_bytes(n, nnz, k, mixed, heavy_nnz=0):
-    """B_alg = row_ptr + (col + val) per nonzero + one gathered row per nonzero
-    (rounded up to 32-byte sectors) + the two previous iterates' own rows read
-    and the new row written (float32 master) [+ the bfloat16 gather copy
-    written in the mixed form].  Nonzeros of chunked rows are streamed by the
-    heavy kernel and excluded here when ``heavy_nnz`` is given."""
+    """Algorithmic bytes of one iteration: B_alg = row_ptr + (col + val) per
+    nonzero + one gathered row per nonzero (rounded up to 32-byte sectors) +
+    the two previous iterates' own rows read and the new row written (float32
+    master) [+ the bfloat16 gather copy written in the mixed form].  With
+    ``heavy_nnz`` the nonzeros of chunked rows (streamed by another kernel of
+    the fused form) are left out."""
+    return gather_bytes(n, nnz - heavy_nnz, k, mixed) + update_bytes(n, k, mixed)
+
+
+def gather_bytes(n, nnz, k, mixed):
+    """The product S X: row_ptr, col and val once, one gathered row per nonzero."""
     bg = 2 if mixed else 4
     bv = 2 if mixed else 4
     row = math.ceil(k * bg / 32) * 32
-    m = nnz - heavy_nnz
-    b = 8 * (n + 1) + m * (4 + bv) + m * row + 3 * n * k * 4
-    if mixed:
-        b += n * k * 2
-    return b
+    return 8 * (n + 1) + nnz * (4 + bv) + nnz * row
+
+
+def update_bytes(n, k, mixed):
+    """The row-local update: two previous iterates' rows read, the new row written."""
+    return 3 * n * k * 4 + (n * k * 2 if mixed else 0)
 
 
 def kernel_digest() -> str:
@@ -285,7 +293,7 @@ def run_native(args, ws, rank, local):
     for form in forms:
         mixed = form == "mixed"
         s = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
+                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0)
         s.step(W)
         barrier()
         torch.cuda.synchronize()
@@ -303,7 +311,7 @@ def run_native(args, ws, rank, local):
         f = pkg.objective(rp, col, val, U)
         rep = s.report()
         res[form] = {"ms_total": ms, "it_s": K / (ms / 1000.0), "kt": kt, "f": f, "iters": rep["iters"],
-                     "launches": 1 + K * (3 if kt["heavy_rows"] > 0 else 2)}
+                     "launches": 1 + K * (3 if kt["heavy_rows"] > 0 else 2) + (0 if args.fused else K)}
         sampler_summary[form] = cs.summary()
         s.close()
         del s, U
@@ -313,16 +321,25 @@ def run_native(args, ws, rank, local):
     r = res[head]
     mixed = head == "mixed"
     kt = r["kt"]
-    b_pass = alg_bytes(n, nnz, k, mixed, kt["heavy_nnz"])
     b_iter = alg_bytes(n, nnz, k, mixed, 0)
+    tag = "true" if mixed else "false"
+    if args.fused:
+        b_pass = alg_bytes(n, nnz, k, mixed, kt["heavy_nnz"])
+        kname = f"fista_pass_kernel<32,{tag},false>"
+    else:
+        b_pass = gather_bytes(n, nnz, k, mixed)
+        kname = f"spmm_kernel<32,{tag}>"
     achieved = b_pass / (kt["pass_ms"] / 1000.0) / 1e9
-    traffic = traffic_for(head)
+    traffic = traffic_for(head + ("_fused" if args.fused else ""))
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": "fista_pass_kernel<32,%s,false>" % ("true" if mixed else "false"),
-            "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
-            "pass_ms": kt["pass_ms"], "heavy_ms": kt["heavy_ms"], "fold_ms": kt["fold_ms"],
-            "iteration_alg_bytes": b_iter,
+            "traffic": traffic, "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
+            "pass_ms": kt["pass_ms"], "heavy_ms": kt["heavy_ms"], "update_ms": kt["update_ms"],
+            "fold_ms": kt["fold_ms"], "iteration_alg_bytes": b_iter,
             "iteration_frac": b_iter / (r["ms_total"] / K / 1000.0) / 1e9 / hbm}
+    if not args.fused:
+        ub = update_bytes(n, k, mixed)
+        roof["update_kernel"] = {"alg_bytes_per_launch": ub, "ms": kt["update_ms"],
+                                 "achieved": ub / (kt["update_ms"] / 1000.0) / 1e9 if kt["update_ms"] else None}
     clocks = sampler_summary[head]
 
     # end to end through the public API from pinned host buffers
@@ -353,9 +370,11 @@ def run_native(args, ws, rank, local):
                    "n": n, "k": k, "nnz": nnz, "max_degree": max_deg, "seed": args.seed,
                    "l2": "inputs larger than L2 (S 16 GB, iterate 9 GB); no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "iteration_form": "fused" if args.fused else "split",
                    "gen_seconds": round(gen_s, 1)},
         "forms": {f: {"it_s": res[f]["it_s"], "ms_per_step": res[f]["ms_total"] / K, "objective": res[f]["f"],
                       "pass_ms": res[f]["kt"]["pass_ms"], "heavy_ms": res[f]["kt"]["heavy_ms"],
+                      "update_ms": res[f]["kt"]["update_ms"],
                       "fold_ms": res[f]["kt"]["fold_ms"], "iters_done": res[f]["iters"],
                       "clocks": sampler_summary[f]} for f in res},
         "equal_objective": eq,
@@ -400,7 +419,7 @@ def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
     for h, d in ((h_rp, d_rp), (h_col, d_col), (h_val, d_val), (h_U0, d_U0)):
         d.copy_(h, non_blocking=True)
     s = pkg.Solver(d_rp, d_col, d_val, d_U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                   precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
+                   precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0)
     losses = []
     for _ in range(K):
         losses.append(s.step(1)["f"])

@@ -116,7 +116,9 @@ typedef struct cluster_options {
   double tol;          /* stopping tolerance (default 0)                        */
   int64_t max_iter;    /* iteration cap, >= 1 (default 1000)                    */
   int32_t graph_chunk; /* iterations per captured CUDA graph (default 16)      */
-  int32_t _pad;
+  int32_t fused_pass;  /* 0 = split iteration (gather kernel + streaming update
+                          kernel, default); 1 = one fused kernel per iteration.
+                          Same arithmetic; the Gram partial order differs.      */
 } cluster_options;
 
 /* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */
@@ -173,9 +175,10 @@ CLUSTER_API cluster_status cluster_enqueue(cluster_ctx* ctx, int64_t iters);
  * fold = the float64 fold.  heavy_nnz is the number of nonzeros the heavy
  * kernel streams per iteration (the pass kernel streams nnz - heavy_nnz). */
 typedef struct cluster_kernel_times {
-  double pass_ms;
-  double heavy_ms;
+  double pass_ms;      /* split: the gather kernel S*X; fused: the fused pass    */
+  double heavy_ms;     /* split: chunk-sum kernel; fused: chunk partial kernel   */
   double fold_ms;
+  double update_ms;    /* split: the streaming update kernel; fused: 0          */
   double total_ms;     /* first event to last event                            */
   int64_t launches;    /* iterations timed                                     */
   int64_t heavy_nnz;

@@ -107,7 +107,10 @@ struct PassArgs {
   float* X1;
   __nv_bfloat16* XS0;        // bfloat16 gather copies (mixed precision)
   __nv_bfloat16* XS1;
-  float* Zp;                 // n x KP: S Xbar^{pass-1}, replaced by S Xbar^{pass}
+  float* Zp;                 // fused pass: n x KP S Xbar^{pass-1}, replaced by S Xbar^{pass}
+  float* Z0;                 // split pass: S Xbar^j in Z_{(j+1)&1}, n x KP float32
+  float* Z1;
+  unsigned long long* work;  // split pass: work counter of spmm_kernel (reset by the fold)
   const float* Gy;           // KP x KP float32, G(Y) minus its mean entry
   float* gram_part;          // [gridDim.x][2][KP][KP]
   double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite
@@ -319,9 +322,14 @@ __host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
 // results into slot `slot` of gram_part / sc_part.  `pass` is the index of the
 // newest iterate (the buffer parity), or the evaluated buffer when EVAL.
 // EVAL: objective-only (z = S X, p_i, Gram of X; no update).
-template <int KP, bool MIXED, bool EVAL>
+template <int KP, bool MIXED, bool EVAL, bool SPLIT = false>
 __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int64_t p0, int64_t p1, int slot,
                                            float* smem) {
+  static_assert(!(SPLIT && EVAL), "the split update has no objective-only form");
+  // SPLIT: rows in index order, z_i read from the product spmm_kernel stored
+  // (Z_{(pass+1)&1}), the previous product from Z_{pass&1}; nothing gathered here
+  const float* Zcur = ((pass + 1) & 1) ? a.Z1 : a.Z0;
+  const float* Zprv = (pass & 1) ? a.Z1 : a.Z0;
   using L = Lay<KP>;
   FistaState* st = a.st;
   const float beta = EVAL ? 0.f : (float)st->beta;
@@ -372,21 +380,24 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   double tr_acc = 0.0, pg_acc = 0.0;
   int bad = 0;
 
-  int64_t next_row = (p0 + team < p1) ? (a.order ? (int64_t)a.order[p0 + team] : p0 + team) : 0;
+  const int32_t* order = SPLIT ? nullptr : a.order;
+  int64_t next_row = (p0 + team < p1) ? (order ? (int64_t)order[p0 + team] : p0 + team) : 0;
   for (int64_t base = p0; base < p1; base += L::R) {
     const int64_t pos = base + team;
     const bool active = pos < p1;
     const int64_t row = active ? next_row : 0;
     {  // row id of the next tile, fetched one tile ahead
       const int64_t np = pos + L::R;
-      next_row = (np < p1) ? (a.order ? (int64_t)a.order[np] : np) : 0;
+      next_row = (np < p1) ? (order ? (int64_t)order[np] : np) : 0;
     }
     float acc[L::VEC];
 #pragma unroll
     for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
 
     int64_t lo = 0, hi = 0;
-    if (active && pos < a.n_heavy) {
+    if constexpr (SPLIT) {
+      load_row<L::VEC>(Zcur + row * KP + f0, acc);
+    } else if (active && pos < a.n_heavy) {
       // chunked row: sum the partial products in chunk order
       const int64_t c0 = a.chunk_ptr[pos], c1 = a.chunk_ptr[pos + 1];
       for (int64_t c = c0; c < c1; ++c) {
@@ -405,11 +416,13 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
     float qv[L::VEC], zp[L::VEC];
     if constexpr (!EVAL) {
       load_row<L::VEC>(Q + row * KP + f0, qv);
-      load_row<L::VEC>(a.Zp + row * KP + f0, zp);
+      load_row<L::VEC>((SPLIT ? Zprv : a.Zp) + row * KP + f0, zp);
     }
-    const int nb = (int)((hi - lo + L::NB - 1) / L::NB);
-    const int batches = __reduce_max_sync(kFull, nb);
-    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+    if constexpr (!SPLIT) {
+      const int nb = (int)((hi - lo + L::NB - 1) / L::NB);
+      const int batches = __reduce_max_sync(kFull, nb);
+      gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+    }
 
     float d = 0.f;
 #pragma unroll
@@ -459,7 +472,7 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
       if (active && lt == 0) pg_acc += (double)pg;
       if (active) {
         store_row<L::VEC>(Q + row * KP + f0, x);
-        store_row<L::VEC>(a.Zp + row * KP + f0, acc);
+        if constexpr (!SPLIT) store_row<L::VEC>(a.Zp + row * KP + f0, acc);
         if constexpr (MIXED) store_row_bf16<L::VEC>(XSo + row * KP + f0, x);
       }
       // next pass's extrapolated row y^{n+1} = xbar^n + beta_{n+1} (xbar^n - xbar^{n-1}),
@@ -579,6 +592,107 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
   pass_range<KP, MIXED, EVAL>(a, pass, p0, p1, blockIdx.x, smem);
 }
 
+// Split iteration, step 1: z_i = (S Xbar^{pass})_i for every row, stored in
+// Z_{(pass+1)&1}, plus the partial products of chunked rows.  Pure gather, no
+// per-tile barrier: warps take work units from a global counter (units of
+// TPW chunks first, then units of TPW * kRowsPerUnit consecutive positions of
+// the degree order, so the teams of a warp have equal trip counts).  Each
+// row's result is computed by exactly one team in a fixed order, so the
+// dynamic schedule does not change any value.
+constexpr int kRowsPerUnit = 4;
+
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT) spmm_kernel(PassArgs a) {
+  using L = Lay<KP>;
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  const float* P = (pass & 1) ? a.X1 : a.X0;
+  const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
+  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
+  const int lane = threadIdx.x & 31;
+  const int tiw = lane / L::T, lt = lane % L::T, f0 = lt * L::VEC;
+  const int64_t n_cu = (a.n_chunks + L::TPW - 1) / L::TPW;
+  const int64_t light = a.n - a.n_heavy;
+  const int64_t n_ru = (light + (int64_t)L::TPW * kRowsPerUnit - 1) / ((int64_t)L::TPW * kRowsPerUnit);
+  for (;;) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(a.work, 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    if ((int64_t)u >= n_cu + n_ru) break;
+    if ((int64_t)u < n_cu) {
+      const int64_t c = (int64_t)u * L::TPW + tiw;
+      const bool act = c < a.n_chunks;
+      const int64_t lo = act ? a.chunk_e0[c] : 0, hi = act ? a.chunk_e1[c] : 0;
+      float acc[L::VEC];
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+      const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
+      gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+      if (act) store_row<L::VEC>(a.hv_part + c * KP + f0, acc);
+    } else {
+      const int64_t base = a.n_heavy + ((int64_t)u - n_cu) * L::TPW * kRowsPerUnit;
+      int64_t nrow = (base + tiw < a.n) ? (int64_t)a.order[base + tiw] : 0;
+#pragma unroll 1
+      for (int m = 0; m < kRowsPerUnit; ++m) {
+        const int64_t pos = base + (int64_t)m * L::TPW + tiw;
+        const bool act = pos < a.n;
+        const int64_t row = nrow;
+        const int64_t npos = pos + L::TPW;
+        nrow = (m + 1 < kRowsPerUnit && npos < a.n) ? (int64_t)a.order[npos] : 0;
+        const int64_t lo = act ? a.row_ptr[row] : 0, hi = act ? a.row_ptr[row + 1] : 0;
+        float acc[L::VEC];
+#pragma unroll
+        for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+        const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
+        gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+        if (act) store_row<L::VEC>(Zc + row * KP + f0, acc);
+      }
+    }
+  }
+}
+
+// Split iteration, step 2: z of every chunked row = sum of its chunk partials
+// in chunk order.
+template <int KP>
+__global__ void __launch_bounds__(256) heavy_finalize_kernel(PassArgs a) {
+  using L = Lay<KP>;
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t teams = (int64_t)gridDim.x * blockDim.x / L::T;
+  const int lt = (int)(t % L::T), f0 = lt * L::VEC;
+  for (int64_t p = t / L::T; p < a.n_heavy; p += teams) {
+    const int64_t row = a.order[p];
+    float acc[L::VEC];
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+    for (int64_t c = a.chunk_ptr[p]; c < a.chunk_ptr[p + 1]; ++c) {
+      float pv[L::VEC];
+      load_row<L::VEC>(a.hv_part + c * KP + f0, pv);
+#pragma unroll
+      for (int q = 0; q < L::VEC; ++q) acc[q] += pv[q];
+    }
+    store_row<L::VEC>(Zc + row * KP + f0, acc);
+  }
+}
+
+// Split iteration, step 3: the row-local update (extrapolation, y G, step,
+// projection, writes, Gram and scalar partials) over rows in index order,
+// block b taking rows [b n / grid, (b+1) n / grid) and partial slot b.
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) update_kernel(PassArgs a) {
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  const int64_t p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
+  const int64_t p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  extern __shared__ __align__(16) float smem[];
+  pass_range<KP, MIXED, false, true>(a, pass, p0, p1, blockIdx.x, smem);
+}
+
 // Partial products of chunked (very high degree) rows: hv_part[c] = sum over
 // chunk c's nonzeros of s_ij * xbar_j.  Teams stride over chunks in rounds so
 // that the gather stays warp-uniform.  EVAL: for an objective-only pass over
@@ -623,6 +737,7 @@ struct FoldArgs {
   int32_t eval;             // 1: objective-only pass (Gram of the evaluated iterate only)
   int32_t eval_init;        // 1: also seed the solver (G(Y^1) = Gram of Xbar^0, gram2_cur)
   int32_t pad_;
+  unsigned long long* work; // spmm work counter, reset for the next pass (may be null)
   double* A;                // KP x KP float64: Gram of the newest iterate (scratch)
   double* G;                // KP x KP float64: Gram of the next extrapolated point (scratch)
   float* Gy;                // KP x KP float32 for the next pass
@@ -754,7 +869,10 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
     }
     if (tid == 0) st->shift = mean;
   }
-  if (tid == 0) st->ticket = 0u;
+  if (tid == 0) {
+    st->ticket = 0u;
+    if (f.work) *f.work = 0ull;
+  }
 }
 
 }  // namespace fc

@@ -88,6 +88,39 @@ struct KPOps {
     else if (mixed) heavy_kernel<KP, true, false><<<grid, L::NT, 0, s>>>(a);
     else heavy_kernel<KP, false, false><<<grid, L::NT, 0, s>>>(a);
   }
+  static int occ_spmm(bool mixed) {
+    int occ = 0;
+    if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_kernel<KP, true>, L::NT, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_kernel<KP, false>, L::NT, 0);
+    return occ < 1 ? 1 : occ;
+  }
+  static int occ_update(bool mixed) {
+    int occ = 0;
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, true>, L::NT, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, false>, L::NT, smem);
+    return occ < 1 ? 1 : occ;
+  }
+  static cudaError_t setup_update_attr() {
+    const int smem = (int)pass_smem_bytes<KP>(false);
+    cudaError_t e = cudaFuncSetAttribute(update_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(update_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
+  static void launch_spmm(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+    if (mixed) spmm_kernel<KP, true><<<grid, L::NT, 0, s>>>(a);
+    else spmm_kernel<KP, false><<<grid, L::NT, 0, s>>>(a);
+  }
+  static void launch_finalize(const PassArgs& a, cudaStream_t s) {
+    const int64_t threads = a.n_heavy * L::T;
+    int grid = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    heavy_finalize_kernel<KP><<<grid < 1 ? 1 : grid, 256, 0, s>>>(a);
+  }
+  static void launch_update(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (mixed) update_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
+    else update_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
+  }
   static void launch_fold(const FoldArgs& f, cudaStream_t s) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
     fold_kernel<KP><<<(nent + 255) / 256, 256, 0, s>>>(f);
@@ -130,6 +163,28 @@ static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, boo
   FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static int kp_occ_spmm(int KP, bool mixed) {
+  int o = 1;
+  FC_DISPATCH(KP, o = Ops::occ_spmm(mixed));
+  return o;
+}
+static int kp_occ_update(int KP, bool mixed) {
+  int o = 1;
+  FC_DISPATCH(KP, o = Ops::occ_update(mixed));
+  return o;
+}
+static cudaError_t kp_setup_update_attr(int KP) {
+  cudaError_t e = cudaSuccess;
+  FC_DISPATCH(KP, e = Ops::setup_update_attr());
+  return e;
+}
+static void kp_launch_spmm(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_spmm(a, grid, mixed, s));
+}
+static void kp_launch_finalize(int KP, const PassArgs& a, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_finalize(a, s)); }
+static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, s));
+}
 
 __global__ void set_limit_kernel(FistaState* st, int64_t iters) { st->limit = st->pass + iters; }
 
@@ -177,7 +232,7 @@ static void ctx_free(cluster_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
-                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st};
+                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -202,6 +257,9 @@ static PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
   a.XS0 = c->XS[0];
   a.XS1 = c->XS[1];
   a.Zp = c->Zp;
+  a.Z0 = c->Z[0];
+  a.Z1 = c->Z[1];
+  a.work = c->work;
   a.Gy = c->Gy;
   a.gram_part = c->gram_part;
   a.sc_part = c->sc_part;
@@ -218,7 +276,8 @@ static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
   f.st = c->st;
   f.gram_part = c->gram_part;
   f.sc_part = c->sc_part;
-  f.parts = c->parts;
+  f.parts = (!eval && c->split) ? c->parts_upd : c->parts;
+  f.work = (!eval && c->split) ? c->work : nullptr;
   f.eval = eval;
   f.eval_init = eval_init;
   f.A = c->A[0];
@@ -230,8 +289,14 @@ static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
 // Enqueue one iteration (heavy chunks, fused pass, fold).
 static void enqueue_pass(const cluster_ctx* c, cudaStream_t s) {
   PassArgs a = make_pass_args(c, false);
-  if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
-  kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
+  if (c->split) {
+    kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+    if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
+    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, s);
+  } else {
+    if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
+    kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
+  }
   kp_launch_fold(c->KP, make_fold_args(c, 0, 0), s);
 }
 
@@ -548,6 +613,14 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   if (parts < 1) parts = 1;
   c->parts = (int)parts;
   c->heavy_grid = sms * occ;
+  c->split = opt.fused_pass == 0;
+  if (c->split) {
+    FC_CUDA(kp_setup_update_attr(c->KP));
+    c->spmm_grid = sms * kp_occ_spmm(c->KP, c->mixed);
+    int64_t pu = (int64_t)sms * kp_occ_update(c->KP, c->mixed);
+    if (pu > tiles) pu = tiles;
+    c->parts_upd = (int)std::max<int64_t>(1, pu);
+  }
   // rows above H nonzeros (about 64 KB of gathered float32 data) are chunked
   c->heavy_H = std::max<int64_t>(64, 16384 / c->KP);
   c->row_cost = 6;
@@ -557,8 +630,17 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   const size_t nk = (size_t)n * c->KP;
   FC_CUDA(cudaMalloc(&c->X[0], sizeof(float) * nk));
   FC_CUDA(cudaMalloc(&c->X[1], sizeof(float) * nk));
-  FC_CUDA(cudaMalloc(&c->Zp, sizeof(float) * nk));
-  FC_CUDA(cudaMemsetAsync(c->Zp, 0, sizeof(float) * nk, s));
+  if (c->split) {
+    FC_CUDA(cudaMalloc(&c->Z[0], sizeof(float) * nk));
+    FC_CUDA(cudaMalloc(&c->Z[1], sizeof(float) * nk));
+    FC_CUDA(cudaMemsetAsync(c->Z[0], 0, sizeof(float) * nk, s));
+    FC_CUDA(cudaMemsetAsync(c->Z[1], 0, sizeof(float) * nk, s));
+    FC_CUDA(cudaMalloc(&c->work, sizeof(unsigned long long)));
+    FC_CUDA(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), s));
+  } else {
+    FC_CUDA(cudaMalloc(&c->Zp, sizeof(float) * nk));
+    FC_CUDA(cudaMemsetAsync(c->Zp, 0, sizeof(float) * nk, s));
+  }
   if (c->mixed) {
     FC_CUDA(cudaMalloc(&c->XS[0], sizeof(__nv_bfloat16) * nk));
     FC_CUDA(cudaMalloc(&c->XS[1], sizeof(__nv_bfloat16) * nk));
@@ -567,8 +649,9 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   FC_CUDA(cudaMalloc(&c->A[0], sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->A[1], sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->Gy, sizeof(float) * e2));
-  FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * c->parts));
-  FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * c->parts));
+  const int slots = std::max(c->parts, c->parts_upd);
+  FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * slots));
+  FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * slots));
   FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
 
   // Xbar^0 = U0 in buffer 0; buffer 1 starts as a copy (momentum is 0 for the first two passes)
@@ -624,7 +707,8 @@ static cluster_status finalize_loss(cluster_ctx* c) {
   return CLUSTER_OK;
 }
 
-// checkpoint layout: header, FistaState, Gy (float32 KP^2), X0, X1, Zp [, XS0, XS1]
+// checkpoint layout: header, FistaState, Gy (float32 KP^2), X0, X1, Z0, Z1 (split) or Zp (fused)
+// [, XS0, XS1]
 struct StateHeader {
   uint64_t magic;
   int64_t n;
@@ -634,7 +718,7 @@ static const uint64_t kStateMagic = 0x46434C5553543031ull;  // "FCLUST01"
 
 static size_t state_bytes(const cluster_ctx* c) {
   const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
-  size_t b = sizeof(StateHeader) + sizeof(FistaState) + e2 * sizeof(float) + 3 * nk * sizeof(float);
+  size_t b = sizeof(StateHeader) + sizeof(FistaState) + e2 * sizeof(float) + (c->split ? 4 : 3) * nk * sizeof(float);
   if (c->mixed) b += 2 * nk * sizeof(__nv_bfloat16);
   return b;
 }
@@ -704,6 +788,7 @@ extern "C" void cluster_options_default(cluster_options* opt) {
   opt->tol = 0.0;
   opt->max_iter = 1000;
   opt->graph_chunk = 16;
+  opt->fused_pass = 0;
 }
 
 extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
@@ -748,30 +833,52 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
   FC_CUDA(cudaSetDevice(c->dev));
   memset(out, 0, sizeof(*out));
   cudaStream_t s = c->stream;
-  std::vector<cudaEvent_t> ev((size_t)(4 * iters));
+  std::vector<cudaEvent_t> ev((size_t)(5 * iters));
   for (auto& e : ev) FC_CUDA(cudaEventCreate(&e));
   set_limit_kernel<<<1, 1, 0, s>>>(c->st, iters);
   PassArgs a = make_pass_args(c, false);
   const FoldArgs f = make_fold_args(c, 0, 0);
+  // events: [0] start, [1] after the gather (split) / chunk kernel (fused), [2] after the chunk sums (split) /
+  // fused pass, [3] after the update (split), [4] after the fold
   for (int64_t i = 0; i < iters; ++i) {
-    cudaEvent_t* e = &ev[(size_t)(4 * i)];
+    cudaEvent_t* e = &ev[(size_t)(5 * i)];
     cudaEventRecord(e[0], s);
-    if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
-    cudaEventRecord(e[1], s);
-    kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
-    cudaEventRecord(e[2], s);
-    kp_launch_fold(c->KP, f, s);
+    if (c->split) {
+      kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+      cudaEventRecord(e[1], s);
+      if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
+      cudaEventRecord(e[2], s);
+      kp_launch_update(c->KP, a, c->parts_upd, c->mixed, s);
+    } else {
+      if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
+      cudaEventRecord(e[1], s);
+      kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
+      cudaEventRecord(e[2], s);
+    }
     cudaEventRecord(e[3], s);
+    kp_launch_fold(c->KP, f, s);
+    cudaEventRecord(e[4], s);
   }
   cudaError_t err = cudaStreamSynchronize(s);
   if (err == cudaSuccess) err = cudaGetLastError();
-  double th = 0, tp = 0, tf = 0;
+  double th = 0, tp = 0, tf = 0, tu = 0;
   float ms = 0.f;
   for (int64_t i = 0; i < iters && err == cudaSuccess; ++i) {
-    cudaEvent_t* e = &ev[(size_t)(4 * i)];
-    cudaEventElapsedTime(&ms, e[0], e[1]); th += ms;
-    cudaEventElapsedTime(&ms, e[1], e[2]); tp += ms;
-    cudaEventElapsedTime(&ms, e[2], e[3]); tf += ms;
+    cudaEvent_t* e = &ev[(size_t)(5 * i)];
+    float m01, m12, m23, m34;
+    cudaEventElapsedTime(&m01, e[0], e[1]);
+    cudaEventElapsedTime(&m12, e[1], e[2]);
+    cudaEventElapsedTime(&m23, e[2], e[3]);
+    cudaEventElapsedTime(&m34, e[3], e[4]);
+    if (c->split) {
+      tp += m01;
+      th += m12;
+      tu += m23;
+    } else {
+      th += m01;
+      tp += m12;
+    }
+    tf += m34;
   }
   if (err == cudaSuccess) {
     cudaEventElapsedTime(&ms, ev.front(), ev.back());
@@ -785,6 +892,7 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
   out->pass_ms = tp / iters;
   out->heavy_ms = th / iters;
   out->fold_ms = tf / iters;
+  out->update_ms = tu / iters;
   out->launches = iters;
   out->heavy_rows = c->n_heavy;
   out->heavy_nnz = c->heavy_nnz;
@@ -846,16 +954,29 @@ extern "C" cluster_status cluster_get_state(cluster_ctx* c, void* buf, size_t by
   if (bytes < state_bytes(c)) FC_EINVAL("state buffer too small (%zu < %zu)", bytes, state_bytes(c));
   FC_CUDA(cudaSetDevice(c->dev));
   char* p = (char*)buf;
-  StateHeader hd{kStateMagic, c->n, c->k, c->KP, c->mixed ? 1 : 0, 0};
+  StateHeader hd{kStateMagic, c->n, c->k, c->KP, c->mixed ? 1 : 0, c->split ? 1 : 0};
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
   const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
   struct Seg {
     const void* src;
     size_t b;
-  } segs[] = {{c->st, sizeof(FistaState)}, {c->Gy, e2 * 4},   {c->X[0], nk * 4},
-              {c->X[1], nk * 4},          {c->Zp, nk * 4},   {c->XS[0], nk * 2}, {c->XS[1], nk * 2}};
-  const int nseg = c->mixed ? 7 : 5;
+  } segs[8];
+  int nseg = 0;
+  segs[nseg++] = {c->st, sizeof(FistaState)};
+  segs[nseg++] = {c->Gy, e2 * 4};
+  segs[nseg++] = {c->X[0], nk * 4};
+  segs[nseg++] = {c->X[1], nk * 4};
+  if (c->split) {
+    segs[nseg++] = {c->Z[0], nk * 4};
+    segs[nseg++] = {c->Z[1], nk * 4};
+  } else {
+    segs[nseg++] = {c->Zp, nk * 4};
+  }
+  if (c->mixed) {
+    segs[nseg++] = {c->XS[0], nk * 2};
+    segs[nseg++] = {c->XS[1], nk * 2};
+  }
   for (int i = 0; i < nseg; ++i) {
     FC_CUDA(cudaMemcpyAsync(p, segs[i].src, segs[i].b, cudaMemcpyDeviceToHost, c->stream));
     p += segs[i].b;
@@ -872,8 +993,9 @@ extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, siz
   const char* p = (const char*)buf;
   StateHeader hd;
   memcpy(&hd, p, sizeof(hd));
-  if (hd.magic != kStateMagic || hd.n != c->n || hd.k != c->k || hd.KP != c->KP || hd.mixed != (c->mixed ? 1 : 0))
-    FC_EINVAL("state does not match this context (n, k or precision differ)");
+  if (hd.magic != kStateMagic || hd.n != c->n || hd.k != c->k || hd.KP != c->KP || hd.mixed != (c->mixed ? 1 : 0) ||
+      hd.pad != (c->split ? 1 : 0))
+    FC_EINVAL("state does not match this context (n, k, precision or iteration form differ)");
   p += sizeof(hd);
   FistaState fs;
   memcpy(&fs, p, sizeof(fs));
@@ -882,9 +1004,22 @@ extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, siz
   struct Seg {
     void* dst;
     size_t b;
-  } segs[] = {{c->st, sizeof(FistaState)}, {c->Gy, e2 * 4},   {c->X[0], nk * 4},
-              {c->X[1], nk * 4},          {c->Zp, nk * 4},   {c->XS[0], nk * 2}, {c->XS[1], nk * 2}};
-  const int nseg = c->mixed ? 7 : 5;
+  } segs[8];
+  int nseg = 0;
+  segs[nseg++] = {c->st, sizeof(FistaState)};
+  segs[nseg++] = {c->Gy, e2 * 4};
+  segs[nseg++] = {c->X[0], nk * 4};
+  segs[nseg++] = {c->X[1], nk * 4};
+  if (c->split) {
+    segs[nseg++] = {c->Z[0], nk * 4};
+    segs[nseg++] = {c->Z[1], nk * 4};
+  } else {
+    segs[nseg++] = {c->Zp, nk * 4};
+  }
+  if (c->mixed) {
+    segs[nseg++] = {c->XS[0], nk * 2};
+    segs[nseg++] = {c->XS[1], nk * 2};
+  }
   for (int i = 0; i < nseg; ++i) {
     const void* src = (i == 0) ? (const void*)&fs : (const void*)p;
     FC_CUDA(cudaMemcpyAsync(segs[i].dst, src, segs[i].b, cudaMemcpyHostToDevice, c->stream));

@@ -39,7 +39,12 @@ struct cluster_ctx {
   // iterate state
   float* X[2] = {nullptr, nullptr};
   __nv_bfloat16* XS[2] = {nullptr, nullptr};
-  float* Zp = nullptr;
+  float* Zp = nullptr;                  // fused iteration: stored product S Xbar^{n-1}
+  float* Z[2] = {nullptr, nullptr};     // split iteration: S Xbar^j in Z[(j+1)&1]
+  unsigned long long* work = nullptr;   // split iteration: gather kernel work counter
+  bool split = true;
+  int parts_upd = 1;                    // blocks (and partial slots) of the update kernel
+  int spmm_grid = 1;
   double* A[2] = {nullptr, nullptr};  // float64 fold scratch: Gram of Xbar^n, Gram of Y^{n+1}
   float* Gy = nullptr;                 // float32 G(Y) (minus its mean) read by the next pass
   float* gram_part = nullptr;

@@ -102,6 +102,22 @@ def test_fifty_iterations_match_oracle(spec, k, accel):
     assert np.all(U >= 0) and np.allclose(U.sum(1), 1.0, atol=1e-5)
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_split_and_fused_iterations_agree_with_oracle(fused, prec):
+    spec = synth.GraphSpec("dcsbm", 12000, 32, 23, mean_deg=30.0)
+    rp, c, v = synth.make_graph(spec)
+    S = to_scipy(rp, c, v, spec.n)
+    U0 = synth.dirichlet_u0(spec.n, 32, 23)
+    s, _ = _solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50, fused_pass=fused, precision=prec)
+    rep = s.solve()
+    o = oracle.fista(S, U0.numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=50, stop="none")
+    tol = TOL_U if prec == 0 else 1e-4
+    assert maxabs(s.get_U().cpu().numpy(), o.U) <= tol
+    f_ref = oracle.objective_trace(S, o.U)
+    assert abs(rep["f"] - f_ref) <= (TOL_F if prec == 0 else 1e-5) * f_ref
+
+
 def test_heavy_rows_are_chunked_and_exact():
     # a hub row adjacent to everything exercises the chunked-row path
     n, k = 3000, 32
