@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 
 METRIC = "PG iters/s, mixed vs FP32, at equal objective (n=70M,k=32); serving p99 latency"
 UNIT = "iter/s"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_fista_pass.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k32_n70M.json")
 PASS_SRC = os.path.join(ROOT, "paper_2506_04045_b300", "csrc", "pass_kernels.cuh")
 
 
@@ -155,13 +155,15 @@ def kernel_digest() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def traffic_for(form: str):
+def traffic_for(form: str, workload: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu capture,
+    or None when the capture is of another workload or an older kernel source."""
     try:
         with open(TRAFFIC_FILE) as fh:
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("kernel_sha") != kernel_digest():
+    if d.get("kernel_sha") != kernel_digest() or d.get("workload") != workload:
         return None
     ent = d.get(form)
     return None if ent is None else ent.get("bytes_per_launch")
@@ -330,7 +332,8 @@ def run_native(args, ws, rank, local):
         b_pass = gather_bytes(n, nnz, k, mixed)
         kname = f"spmm_kernel<32,{tag}>"
     achieved = b_pass / (kt["pass_ms"] / 1000.0) / 1e9
-    traffic = traffic_for(head + ("_fused" if args.fused else ""))
+    traffic = traffic_for(head + ("_fused" if args.fused else ""),
+                          f"dcsbm n={n} k={k} nnz={nnz} seed={args.seed}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
             "pass_ms": kt["pass_ms"], "heavy_ms": kt["heavy_ms"], "update_ms": kt["update_ms"],
