@@ -243,6 +243,38 @@ CLUSTER_API cluster_status cluster_set_state(cluster_ctx* ctx, const void* host_
 CLUSTER_API void cluster_destroy(cluster_ctx* ctx);
 
 /* ------------------------------------------------------------------------ */
+/* Batched solves                                                            */
+/* ------------------------------------------------------------------------ */
+/* A batch advances `count` independent instances (each its own S, k and U0,
+ * all on the current device) together: instances with the same padded cluster
+ * count and precision share one persistent launch per kernel and iteration,
+ * and the iteration sequence is captured in a CUDA graph.  Every instance
+ * runs exactly the arithmetic, row ranges and reduction order it runs alone
+ * (cluster_init with the same options), so its iterates are bit-identical to
+ * a solo run.  S: host array of `count` cluster_csr descriptors (device
+ * arrays); k: host array; U0: host array of `count` device pointers (n_i x
+ * k_i).  opt is shared (fused_pass must be 0).  Inputs are copied as
+ * cluster_init copies them (or borrowed with opt->borrow). */
+typedef struct cluster_batch cluster_batch;
+
+CLUSTER_API cluster_status cluster_batch_create(int32_t count, const cluster_csr* S, const int32_t* k,
+                                                const float* const* U0, const cluster_options* opt,
+                                                void* stream, cluster_batch** out);
+
+/* Enqueue `iters` iterations of every unfinished instance (no host sync). */
+CLUSTER_API cluster_status cluster_batch_enqueue(cluster_batch* b, int64_t iters);
+
+/* Advance every instance by at most `iters` iterations (instances stop on
+ * their own stop rule or max_iter), synchronise, and fill reps[0..count-1]
+ * (may be NULL). */
+CLUSTER_API cluster_status cluster_batch_step(cluster_batch* b, int64_t iters, cluster_report* reps);
+
+/* Copy instance i's output iterate into U_out (device, n_i x k_i). */
+CLUSTER_API cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, float* U_out);
+
+CLUSTER_API void cluster_batch_destroy(cluster_batch* b);
+
+/* ------------------------------------------------------------------------ */
 /* CSR construction (host)                                                   */
 /* ------------------------------------------------------------------------ */
 /* Build the symmetric similarity matrix from an edge list (Example 4.1):

@@ -84,6 +84,12 @@ _SIGS = {
     "cluster_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_destroy": (None, [_P]),
+    "cluster_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(CSR), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(_P), ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
+    "cluster_batch_enqueue": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cluster_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(Report)]),
+    "cluster_batch_get_U": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cluster_batch_destroy": (None, [_P]),
     "cluster_csr_from_edges": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
                                               ctypes.POINTER(CSR)]),
     "cluster_csr_free": (None, [ctypes.POINTER(CSR)]),
@@ -234,6 +240,56 @@ class Solver:
     def close(self) -> None:
         if self._ctx:
             self._lib.cluster_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one cluster_batch over several (row_ptr, col, val, U0) instances
+    (torch CUDA tensors, kept alive by this object)."""
+
+    def __init__(self, instances, stream=None, **opts):
+        self._lib = load()
+        self._keep = list(instances)
+        self.count = len(self._keep)
+        csrs = (CSR * self.count)()
+        ks = (ctypes.c_int32 * self.count)()
+        u0s = (_P * self.count)()
+        self.shapes = []
+        for i, (rp, c, v, U0) in enumerate(self._keep):
+            csrs[i] = make_csr(rp, c, v)
+            ks[i] = int(U0.shape[1])
+            u0s[i] = _ptr(U0)
+            self.shapes.append((int(U0.shape[0]), int(U0.shape[1])))
+        self.options = default_options(**opts)
+        self._ctx = ctypes.c_void_p()
+        check(self._lib.cluster_batch_create(self.count, csrs, ks, u0s, ctypes.byref(self.options),
+                                             _stream_ptr(stream), ctypes.byref(self._ctx)))
+
+    def step(self, iters: int) -> list:
+        reps = (Report * self.count)()
+        check(self._lib.cluster_batch_step(self._ctx, int(iters), reps))
+        return [r.as_dict() for r in reps]
+
+    def enqueue(self, iters: int) -> None:
+        check(self._lib.cluster_batch_enqueue(self._ctx, int(iters)))
+
+    def get_U(self, i: int, out=None):
+        import torch
+        n, k = self.shapes[i]
+        if out is None:
+            out = torch.empty((n, k), dtype=torch.float32, device="cuda")
+        check(self._lib.cluster_batch_get_U(self._ctx, int(i), _ptr(out)))
+        return out
+
+    def close(self) -> None:
+        if self._ctx:
+            self._lib.cluster_batch_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):

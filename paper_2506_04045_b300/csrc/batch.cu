@@ -1,0 +1,318 @@
+// Batched solves: many independent clustering instances of uneven n and k
+// advanced together.  Instances are grouped into classes by padded cluster
+// count and precision; per class and iteration there is one persistent
+// gather launch, one chunk-sum launch, one persistent update launch and one
+// fold launch covering every instance of the class.  The iteration sequence
+// of all classes is captured in a CUDA graph of graph_chunk iterations.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "batch_kernels.cuh"
+#include "solver_impl.h"
+#include "util.h"
+
+using namespace fc;
+
+namespace {
+
+struct BatchClass {
+  int KP = 0;
+  bool mixed = false;
+  std::vector<int> members;  // instance indices
+  // device copies of the per-instance tables
+  PassArgs* d_args = nullptr;
+  FoldArgs* d_folds = nullptr;
+  int64_t* d_unit_base = nullptr;
+  int64_t* d_heavy_base = nullptr;
+  int32_t* d_item_inst = nullptr;
+  int32_t* d_item_slot = nullptr;
+  int32_t* d_parts = nullptr;
+  FistaState** d_states = nullptr;
+  unsigned long long* d_work = nullptr;
+  int n_items = 0;
+  int64_t units = 0, heavy = 0;
+  int spmm_grid = 1, upd_grid = 1, fin_grid = 1;
+  BatchMeta meta{};
+};
+
+template <int KP>
+struct BOps {
+  using L = Lay<KP>;
+  static cudaError_t setup() {
+    const int smem = (int)pass_smem_bytes<KP>(false);
+    cudaError_t e = cudaFuncSetAttribute(batch_update_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_update_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
+  static void grids(BatchClass& bc, int sms) {
+    int o1 = 0, o2 = 0;
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (bc.mixed) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, true>, L::NT, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_update_kernel<KP, true>, L::NT, smem);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, false>, L::NT, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_update_kernel<KP, false>, L::NT, smem);
+    }
+    bc.spmm_grid = sms * std::max(1, o1);
+    const int64_t warps_needed = (bc.units + L::WARPS - 1) / L::WARPS;
+    bc.spmm_grid = (int)std::max<int64_t>(1, std::min<int64_t>(bc.spmm_grid, warps_needed));
+    bc.upd_grid = std::max(1, std::min(sms * std::max(1, o2), bc.n_items));
+    const int64_t fin_threads = bc.heavy * L::T;
+    bc.fin_grid = (int)std::max<int64_t>(1, std::min<int64_t>((fin_threads + 255) / 256, 4096));
+  }
+  static void iteration(const BatchClass& bc, cudaStream_t s) {
+    cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
+    const size_t smem = pass_smem_bytes<KP>(false);
+    if (bc.mixed) batch_spmm_kernel<KP, true><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
+    else batch_spmm_kernel<KP, false><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
+    if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
+    if (bc.mixed) batch_update_kernel<KP, true><<<bc.upd_grid, L::NT, smem, s>>>(bc.meta);
+    else batch_update_kernel<KP, false><<<bc.upd_grid, L::NT, smem, s>>>(bc.meta);
+    batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
+  }
+  static int64_t units(const cluster_ctx* c) { return spmm_units<KP>(c->n, c->n_heavy, c->n_chunks); }
+};
+
+#define FC_BDISPATCH(KPV, CALL)                      \
+  switch (KPV) {                                     \
+    case 2: { using Ops = BOps<2>; CALL; } break;    \
+    case 4: { using Ops = BOps<4>; CALL; } break;    \
+    case 8: { using Ops = BOps<8>; CALL; } break;    \
+    case 16: { using Ops = BOps<16>; CALL; } break;  \
+    case 32: { using Ops = BOps<32>; CALL; } break;  \
+    case 64: { using Ops = BOps<64>; CALL; } break;  \
+    default: { using Ops = BOps<128>; CALL; } break; \
+  }
+
+}  // namespace
+
+struct cluster_batch {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cluster_options opt{};
+  std::vector<cluster_ctx*> inst;
+  std::vector<BatchClass> classes;
+  FistaState** d_all_states = nullptr;
+  FistaState* d_collect = nullptr;
+  std::vector<FistaState> h_collect;
+  int graph_chunk = 16;
+  cudaGraphExec_t graph = nullptr;
+};
+
+static void batch_free(cluster_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto& bc : b->classes) {
+    void* ps[] = {bc.d_args, bc.d_folds, bc.d_unit_base, bc.d_heavy_base, bc.d_item_inst, bc.d_item_slot,
+                  bc.d_parts, bc.d_states, bc.d_work};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+  }
+  if (b->d_all_states) cudaFree(b->d_all_states);
+  if (b->d_collect) cudaFree(b->d_collect);
+  for (cluster_ctx* c : b->inst) ctx_free(c);
+  delete b;
+}
+
+template <typename T>
+static cluster_status upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+  FC_CUDA(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size())));
+  if (!src.empty()) FC_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+  return CLUSTER_OK;
+}
+
+static cluster_status build_class(cluster_batch* b, BatchClass& bc, int sms) {
+  cudaStream_t s = b->stream;
+  std::vector<PassArgs> args;
+  std::vector<FoldArgs> folds;
+  std::vector<int64_t> ubase(1, 0), hbase(1, 0);
+  std::vector<int32_t> item_inst, item_slot, parts;
+  std::vector<FistaState*> states;
+  for (size_t j = 0; j < bc.members.size(); ++j) {
+    const cluster_ctx* c = b->inst[bc.members[j]];
+    args.push_back(make_pass_args(c, false));
+    FoldArgs f = make_fold_args(c, 0, 0);
+    f.work = nullptr;  // the batch zeroes its own counters
+    folds.push_back(f);
+    int64_t u = 0;
+    FC_BDISPATCH(bc.KP, u = Ops::units(c));
+    ubase.push_back(ubase.back() + u);
+    hbase.push_back(hbase.back() + c->n_heavy);
+    parts.push_back(c->parts_upd);
+    for (int sl = 0; sl < c->parts_upd; ++sl) {
+      item_inst.push_back((int32_t)j);
+      item_slot.push_back(sl);
+    }
+    states.push_back(c->st);
+  }
+  bc.units = ubase.back();
+  bc.heavy = hbase.back();
+  bc.n_items = (int)item_inst.size();
+  FC_TRY(upload(&bc.d_args, args, s));
+  FC_TRY(upload(&bc.d_folds, folds, s));
+  FC_TRY(upload(&bc.d_unit_base, ubase, s));
+  FC_TRY(upload(&bc.d_heavy_base, hbase, s));
+  FC_TRY(upload(&bc.d_item_inst, item_inst, s));
+  FC_TRY(upload(&bc.d_item_slot, item_slot, s));
+  FC_TRY(upload(&bc.d_parts, parts, s));
+  FC_TRY(upload(&bc.d_states, states, s));
+  FC_CUDA(cudaMalloc(&bc.d_work, 2 * sizeof(unsigned long long)));
+  FC_CUDA(cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s));
+  BatchMeta& m = bc.meta;
+  m.args = bc.d_args;
+  m.folds = bc.d_folds;
+  m.unit_base = bc.d_unit_base;
+  m.heavy_base = bc.d_heavy_base;
+  m.item_inst = bc.d_item_inst;
+  m.item_slot = bc.d_item_slot;
+  m.parts_upd = bc.d_parts;
+  m.states = bc.d_states;
+  m.m = (int32_t)bc.members.size();
+  m.n_items = bc.n_items;
+  m.work = bc.d_work;
+  FC_CUDA(cudaSetDevice(b->dev));
+  cudaError_t e = cudaSuccess;
+  FC_BDISPATCH(bc.KP, e = Ops::setup());
+  FC_CUDA(e);
+  FC_BDISPATCH(bc.KP, Ops::grids(bc, sms));
+  return CLUSTER_OK;
+}
+
+static void batch_iteration(const cluster_batch* b, cudaStream_t s) {
+  for (const BatchClass& bc : b->classes) FC_BDISPATCH(bc.KP, Ops::iteration(bc, s));
+}
+
+static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const cluster_csr* S, const int32_t* k,
+                                        const float* const* U0, const cluster_options* optp, void* stream) {
+  if (count < 1) FC_EINVAL("count must be >= 1");
+  if (!S || !k || !U0) FC_EINVAL("NULL argument");
+  cluster_options opt;
+  if (optp) opt = *optp;
+  else cluster_options_default(&opt);
+  if (opt.fused_pass) FC_EINVAL("batched solves use the split iteration (fused_pass must be 0)");
+  if (opt.graph_chunk < 1) opt.graph_chunk = 16;
+  b->opt = opt;
+  b->stream = (cudaStream_t)stream;
+  b->graph_chunk = opt.graph_chunk;
+  FC_CUDA(cudaGetDevice(&b->dev));
+  FC_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  std::map<std::pair<int, int>, int> cls;
+  for (int32_t i = 0; i < count; ++i) {
+    cluster_ctx* c = new (std::nothrow) cluster_ctx();
+    if (!c) {
+      set_error("out of host memory");
+      return CLUSTER_ENOMEM;
+    }
+    b->inst.push_back(c);
+    cluster_status st = init_impl(&S[i], k[i], U0[i], &opt, stream, c, false);
+    if (st != CLUSTER_OK) {
+      set_error("instance %d: %s", i, cluster_last_error());
+      return st;
+    }
+    const auto key = std::make_pair(c->KP, c->mixed ? 1 : 0);
+    auto it = cls.find(key);
+    if (it == cls.end()) {
+      BatchClass bc;
+      bc.KP = c->KP;
+      bc.mixed = c->mixed;
+      cls[key] = (int)b->classes.size();
+      b->classes.push_back(bc);
+      it = cls.find(key);
+    }
+    b->classes[it->second].members.push_back(i);
+  }
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
+  for (auto& bc : b->classes) FC_TRY(build_class(b, bc, sms));
+  std::vector<FistaState*> all;
+  for (cluster_ctx* c : b->inst) all.push_back(c->st);
+  FC_TRY(upload(&b->d_all_states, all, b->stream));
+  FC_CUDA(cudaMalloc(&b->d_collect, sizeof(FistaState) * count));
+  b->h_collect.resize(count);
+  FC_CUDA(cudaStreamSynchronize(b->stream));
+  // graph of graph_chunk iterations of every class
+  cudaGraph_t g = nullptr;
+  FC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < b->graph_chunk; ++i) batch_iteration(b, b->cap_stream);
+  FC_CUDA(cudaStreamEndCapture(b->cap_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  FC_CUDA(e);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_batch_create(int32_t count, const cluster_csr* S, const int32_t* k,
+                                               const float* const* U0, const cluster_options* opt, void* stream,
+                                               cluster_batch** out) {
+  clear_error();
+  if (!out) FC_EINVAL("out is NULL");
+  *out = nullptr;
+  cluster_batch* b = new (std::nothrow) cluster_batch();
+  if (!b) {
+    set_error("out of host memory");
+    return CLUSTER_ENOMEM;
+  }
+  cluster_status st = batch_create_impl(b, count, S, k, U0, opt, stream);
+  if (st != CLUSTER_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return CLUSTER_OK;
+}
+
+static cluster_status batch_read(cluster_batch* b, cluster_report* reps) {
+  const int m = (int)b->inst.size();
+  batch_collect_kernel<<<m, 64, 0, b->stream>>>(b->d_all_states, m, b->d_collect);
+  FC_CUDA(cudaGetLastError());
+  FC_CUDA(cudaMemcpyAsync(b->h_collect.data(), b->d_collect, sizeof(FistaState) * m, cudaMemcpyDeviceToHost,
+                          b->stream));
+  FC_CUDA(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < m; ++i) {
+    b->inst[i]->host_st = b->h_collect[i];
+    if (reps) fill_report(b->inst[i], &reps[i]);
+  }
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_batch_enqueue(cluster_batch* b, int64_t iters) {
+  clear_error();
+  if (!b) FC_EINVAL("batch is NULL");
+  if (iters < 0) FC_EINVAL("iters must be >= 0");
+  if (iters == 0) return CLUSTER_OK;
+  FC_CUDA(cudaSetDevice(b->dev));
+  const int m = (int)b->inst.size();
+  batch_set_limit_kernel<<<(m + 255) / 256, 256, 0, b->stream>>>(b->d_all_states, m, iters);
+  const int64_t reps = (iters + b->graph_chunk - 1) / b->graph_chunk;
+  for (int64_t r = 0; r < reps; ++r) FC_CUDA(cudaGraphLaunch(b->graph, b->stream));
+  FC_CUDA(cudaGetLastError());
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_batch_step(cluster_batch* b, int64_t iters, cluster_report* reps) {
+  FC_TRY(cluster_batch_enqueue(b, iters));
+  return batch_read(b, reps);
+}
+
+extern "C" cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, float* U_out) {
+  clear_error();
+  if (!b || !U_out) FC_EINVAL("NULL argument");
+  if (i < 0 || i >= (int32_t)b->inst.size()) FC_EINVAL("instance index %d out of range", i);
+  return cluster_get_U(b->inst[i], U_out);
+}
+
+extern "C" void cluster_batch_destroy(cluster_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+}

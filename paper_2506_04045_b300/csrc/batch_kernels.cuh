@@ -1,0 +1,116 @@
+// Segmented kernels: one launch advances every instance of a batch class (all
+// instances with the same padded cluster count KP and precision) by one
+// iteration.  Each kernel is persistent and takes work from a counter that
+// spans all instances; every unit of work is the same unit the instance's own
+// solver would run (same row ranges, partial slots and reduction order), so a
+// batched instance computes bit for bit what it computes alone.
+#pragma once
+#include "pass_kernels.cuh"
+
+namespace fc {
+
+struct BatchMeta {
+  const PassArgs* args;        // [m] per-instance pass arguments (device)
+  const FoldArgs* folds;       // [m] per-instance fold arguments (device)
+  const int64_t* unit_base;    // [m + 1] prefix sums of gather units
+  const int64_t* heavy_base;   // [m + 1] prefix sums of chunked rows
+  const int32_t* item_inst;    // [n_items] update item -> instance
+  const int32_t* item_slot;    // [n_items] update item -> partial slot (= solo block index)
+  const int32_t* parts_upd;    // [m] update blocks of each instance when run alone
+  FistaState* const* states;   // [m]
+  int32_t m;
+  int32_t n_items;
+  unsigned long long* work;    // [2]: gather units taken, update items taken (zeroed per iteration)
+};
+
+// index j with base[j] <= x < base[j + 1]
+__device__ __forceinline__ int find_segment(const int64_t* base, int m, int64_t x) {
+  int lo = 0, hi = m;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (base[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool instance_idle(const FistaState* st) {
+  const volatile FistaState* vs = st;
+  return vs->done || vs->pass >= vs->limit;
+}
+
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT) batch_spmm_kernel(BatchMeta b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = b.unit_base[b.m];
+  for (;;) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(&b.work[0], 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    if ((int64_t)u >= total) break;
+    const int j = find_segment(b.unit_base, b.m, (int64_t)u);
+    const PassArgs& a = b.args[j];
+    if (instance_idle(a.st)) continue;
+    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+    spmm_unit<KP, MIXED>(a, pass, (int64_t)u - b.unit_base[j], lane);
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) batch_finalize_kernel(BatchMeta b) {
+  using L = Lay<KP>;
+  const int64_t total = b.heavy_base[b.m];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t teams = (int64_t)gridDim.x * blockDim.x / L::T;
+  for (int64_t h = t / L::T; h < total; h += teams) {
+    const int j = find_segment(b.heavy_base, b.m, h);
+    const PassArgs& a = b.args[j];
+    if (instance_idle(a.st)) continue;
+    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+    finalize_row<KP>(a, pass, h - b.heavy_base[j], (int)(t % L::T));
+  }
+}
+
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) batch_update_kernel(BatchMeta b) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= b.n_items) break;
+    const int j = b.item_inst[item];
+    const int slot = b.item_slot[item];
+    const PassArgs& a = b.args[j];
+    if (instance_idle(a.st)) continue;
+    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+    const int parts = b.parts_upd[j];
+    const int64_t p0 = a.n * (int64_t)slot / parts;
+    const int64_t p1 = a.n * (int64_t)(slot + 1) / parts;
+    pass_range<KP, MIXED, false, true>(a, pass, p0, p1, slot, smem);
+    __syncthreads();
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) batch_fold_kernel(BatchMeta b) {
+  constexpr int nb = fold_blocks<KP>(false);
+  fold_body<KP>(b.folds[blockIdx.x / nb], blockIdx.x % nb, nb);
+}
+
+__global__ void batch_set_limit_kernel(FistaState* const* states, int m, int64_t iters) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) states[j]->limit = states[j]->pass + iters;
+}
+
+__global__ void batch_collect_kernel(FistaState* const* states, int m, FistaState* out) {
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  const unsigned* src = reinterpret_cast<const unsigned*>(states[j]);
+  unsigned* dst = reinterpret_cast<unsigned*>(out + j);
+  for (int w = threadIdx.x; w < (int)(sizeof(FistaState) / 4); w += blockDim.x) dst[w] = src[w];
+}
+
+}  // namespace fc

@@ -601,82 +601,102 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
 // dynamic schedule does not change any value.
 constexpr int kRowsPerUnit = 4;
 
+// Work units of one instance's gather: chunk units, then row units.
+template <int KP>
+__host__ __device__ __forceinline__ int64_t spmm_chunk_units(int64_t n_chunks) {
+  return (n_chunks + Lay<KP>::TPW - 1) / Lay<KP>::TPW;
+}
+template <int KP>
+__host__ __device__ __forceinline__ int64_t spmm_units(int64_t n, int64_t n_heavy, int64_t n_chunks) {
+  const int64_t per = (int64_t)Lay<KP>::TPW * kRowsPerUnit;
+  return spmm_chunk_units<KP>(n_chunks) + (n - n_heavy + per - 1) / per;
+}
+
+// One warp processes gather unit u of an instance (see spmm_kernel).
 template <int KP, bool MIXED>
-__global__ void __launch_bounds__(Lay<KP>::NT) spmm_kernel(PassArgs a) {
+__device__ __forceinline__ void spmm_unit(const PassArgs& a, int64_t pass, int64_t u, int lane) {
   using L = Lay<KP>;
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
   const float* P = (pass & 1) ? a.X1 : a.X0;
   const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
   float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
-  const int lane = threadIdx.x & 31;
   const int tiw = lane / L::T, lt = lane % L::T, f0 = lt * L::VEC;
-  const int64_t n_cu = (a.n_chunks + L::TPW - 1) / L::TPW;
-  const int64_t light = a.n - a.n_heavy;
-  const int64_t n_ru = (light + (int64_t)L::TPW * kRowsPerUnit - 1) / ((int64_t)L::TPW * kRowsPerUnit);
+  const int64_t n_cu = spmm_chunk_units<KP>(a.n_chunks);
+  if (u < n_cu) {
+    const int64_t c = u * L::TPW + tiw;
+    const bool act = c < a.n_chunks;
+    const int64_t lo = act ? a.chunk_e0[c] : 0, hi = act ? a.chunk_e1[c] : 0;
+    float acc[L::VEC];
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+    const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
+    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+    if (act) store_row<L::VEC>(a.hv_part + c * KP + f0, acc);
+    return;
+  }
+  const int64_t base = a.n_heavy + (u - n_cu) * L::TPW * kRowsPerUnit;
+  int64_t nrow = (base + tiw < a.n) ? (int64_t)a.order[base + tiw] : 0;
+#pragma unroll 1
+  for (int m = 0; m < kRowsPerUnit; ++m) {
+    const int64_t pos = base + (int64_t)m * L::TPW + tiw;
+    const bool act = pos < a.n;
+    const int64_t row = nrow;
+    const int64_t npos = pos + L::TPW;
+    nrow = (m + 1 < kRowsPerUnit && npos < a.n) ? (int64_t)a.order[npos] : 0;
+    const int64_t lo = act ? a.row_ptr[row] : 0, hi = act ? a.row_ptr[row + 1] : 0;
+    float acc[L::VEC];
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+    const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
+    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
+    if (act) store_row<L::VEC>(Zc + row * KP + f0, acc);
+  }
+}
+
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT) spmm_kernel(PassArgs a) {
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  const int lane = threadIdx.x & 31;
+  const int64_t units = spmm_units<KP>(a.n, a.n_heavy, a.n_chunks);
   for (;;) {
     unsigned long long u = 0;
     if (lane == 0) u = atomicAdd(a.work, 1ull);
     u = __shfl_sync(kFull, u, 0);
-    if ((int64_t)u >= n_cu + n_ru) break;
-    if ((int64_t)u < n_cu) {
-      const int64_t c = (int64_t)u * L::TPW + tiw;
-      const bool act = c < a.n_chunks;
-      const int64_t lo = act ? a.chunk_e0[c] : 0, hi = act ? a.chunk_e1[c] : 0;
-      float acc[L::VEC];
-#pragma unroll
-      for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-      const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
-      gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
-      if (act) store_row<L::VEC>(a.hv_part + c * KP + f0, acc);
-    } else {
-      const int64_t base = a.n_heavy + ((int64_t)u - n_cu) * L::TPW * kRowsPerUnit;
-      int64_t nrow = (base + tiw < a.n) ? (int64_t)a.order[base + tiw] : 0;
-#pragma unroll 1
-      for (int m = 0; m < kRowsPerUnit; ++m) {
-        const int64_t pos = base + (int64_t)m * L::TPW + tiw;
-        const bool act = pos < a.n;
-        const int64_t row = nrow;
-        const int64_t npos = pos + L::TPW;
-        nrow = (m + 1 < kRowsPerUnit && npos < a.n) ? (int64_t)a.order[npos] : 0;
-        const int64_t lo = act ? a.row_ptr[row] : 0, hi = act ? a.row_ptr[row + 1] : 0;
-        float acc[L::VEC];
-#pragma unroll
-        for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-        const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
-        gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
-        if (act) store_row<L::VEC>(Zc + row * KP + f0, acc);
-      }
-    }
+    if ((int64_t)u >= units) break;
+    spmm_unit<KP, MIXED>(a, pass, (int64_t)u, lane);
   }
 }
 
 // Split iteration, step 2: z of every chunked row = sum of its chunk partials
 // in chunk order.
 template <int KP>
+__device__ __forceinline__ void finalize_row(const PassArgs& a, int64_t pass, int64_t p, int lt) {
+  using L = Lay<KP>;
+  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
+  const int f0 = lt * L::VEC;
+  const int64_t row = a.order[p];
+  float acc[L::VEC];
+#pragma unroll
+  for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
+  for (int64_t c = a.chunk_ptr[p]; c < a.chunk_ptr[p + 1]; ++c) {
+    float pv[L::VEC];
+    load_row<L::VEC>(a.hv_part + c * KP + f0, pv);
+#pragma unroll
+    for (int q = 0; q < L::VEC; ++q) acc[q] += pv[q];
+  }
+  store_row<L::VEC>(Zc + row * KP + f0, acc);
+}
+
+template <int KP>
 __global__ void __launch_bounds__(256) heavy_finalize_kernel(PassArgs a) {
   using L = Lay<KP>;
   volatile FistaState* vs = a.st;
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
-  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t teams = (int64_t)gridDim.x * blockDim.x / L::T;
-  const int lt = (int)(t % L::T), f0 = lt * L::VEC;
-  for (int64_t p = t / L::T; p < a.n_heavy; p += teams) {
-    const int64_t row = a.order[p];
-    float acc[L::VEC];
-#pragma unroll
-    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-    for (int64_t c = a.chunk_ptr[p]; c < a.chunk_ptr[p + 1]; ++c) {
-      float pv[L::VEC];
-      load_row<L::VEC>(a.hv_part + c * KP + f0, pv);
-#pragma unroll
-      for (int q = 0; q < L::VEC; ++q) acc[q] += pv[q];
-    }
-    store_row<L::VEC>(Zc + row * KP + f0, acc);
-  }
+  for (int64_t p = t / L::T; p < a.n_heavy; p += teams) finalize_row<KP>(a, pass, p, (int)(t % L::T));
 }
 
 // Split iteration, step 3: the row-local update (extrapolation, y G, step,
@@ -748,7 +768,13 @@ struct FoldArgs {
 // stores G(Y^{n+1}) minus its mean entry in float32 (the mean shift leaves the
 // projection unchanged because rows of Y sum to one: P(v + c 1) = P(v)).
 template <int KP>
-__global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
+__host__ __device__ constexpr int fold_blocks(bool eval) {
+  return ((eval ? 1 : 2) * KP * KP + 255) / 256;
+}
+
+// Block `blk` of the `nblocks` blocks folding one instance (256 threads).
+template <int KP>
+__device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblocks) {
   constexpr int E2 = KP * KP;
   constexpr int BS = KP < 4 ? KP : 4;
   FistaState* st = f.st;
@@ -758,7 +784,7 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   const int64_t nnew = pass + 1;
   const int tid = threadIdx.x;
   const int nent = f.eval ? E2 : 2 * E2;
-  const int e = blockIdx.x * 256 + tid;
+  const int e = blk * 256 + tid;
   if (e < nent) {
     const int m = e / E2, r = (e % E2) / KP, c = e % KP;
     const int src = m * E2 + ((r / BS <= c / BS) ? r * KP + c : c * KP + r);
@@ -769,7 +795,7 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   __threadfence();
   __syncthreads();
   __shared__ int is_last;
-  if (tid == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  if (tid == 0) is_last = (atomicAdd(&st->ticket, 1u) == (unsigned)nblocks - 1);
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -873,6 +899,11 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
     st->ticket = 0u;
     if (f.work) *f.work = 0ull;
   }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
+  fold_body<KP>(f, blockIdx.x, gridDim.x);
 }
 
 }  // namespace fc

@@ -38,7 +38,7 @@ static int padded_k(int k) {
   return kp;
 }
 
-static int grid_for(int64_t work, int threads = 256) {
+int grid_for(int64_t work, int threads = 256) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > 65535LL * 8) b = 65535LL * 8;
@@ -226,7 +226,7 @@ static cluster_status check_csr_args(const cluster_csr* S, int32_t k) {
 // ---------------------------------------------------------------------------
 // context helpers
 // ---------------------------------------------------------------------------
-static void ctx_free(cluster_ctx* c) {
+void ctx_free(cluster_ctx* c) {
   if (!c) return;
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -238,7 +238,7 @@ static void ctx_free(cluster_ctx* c) {
   delete c;
 }
 
-static PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
+PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
   PassArgs a;
   memset(&a, 0, sizeof(a));
   a.row_ptr = c->rp;
@@ -270,7 +270,7 @@ static PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
   return a;
 }
 
-static FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
+FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
   FoldArgs f;
   memset(&f, 0, sizeof(f));
   f.st = c->st;
@@ -309,13 +309,13 @@ static void enqueue_eval(const cluster_ctx* c, int sel, int init, cudaStream_t s
   kp_launch_fold(c->KP, make_fold_args(c, 1, init), s);
 }
 
-static cluster_status read_state(cluster_ctx* c) {
+cluster_status read_state(cluster_ctx* c) {
   FC_CUDA(cudaMemcpyAsync(&c->host_st, c->st, sizeof(FistaState), cudaMemcpyDeviceToHost, c->stream));
   FC_CUDA(cudaStreamSynchronize(c->stream));
   return CLUSTER_OK;
 }
 
-static void fill_report(const cluster_ctx* c, cluster_report* rep) {
+void fill_report(const cluster_ctx* c, cluster_report* rep) {
   if (!rep) return;
   const FistaState& s = c->host_st;
   rep->iters = s.pass;
@@ -532,8 +532,8 @@ static cluster_status sum_squares(const float* val, int64_t nnz, cudaStream_t s,
   return CLUSTER_OK;
 }
 
-static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* optp,
-                                void* stream, cluster_ctx* c) {
+cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* optp,
+                         void* stream, cluster_ctx* c, bool capture) {
   FC_TRY(check_csr_args(S, k));
   if (!U0) FC_EINVAL("U0 is NULL");
   cluster_options opt;
@@ -683,7 +683,7 @@ static cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0
   h.f_iter = 0;
   FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
   FC_CUDA(cudaStreamSynchronize(s));
-  FC_TRY(capture_graph(c));
+  if (capture) FC_TRY(capture_graph(c));
   return CLUSTER_OK;
 }
 
@@ -803,7 +803,7 @@ extern "C" cluster_status cluster_init(const cluster_csr* S, int32_t k, const fl
     set_error("out of host memory");
     return CLUSTER_ENOMEM;
   }
-  cluster_status st = init_impl(S, k, U0, opt, stream, c);
+  cluster_status st = init_impl(S, k, U0, opt, stream, c, true);
   if (st != CLUSTER_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     ctx_free(c);

@@ -55,3 +55,15 @@ struct cluster_ctx {
   int graph_chunk = 16;
   cudaGraphExec_t graph_exec = nullptr;
 };
+
+namespace fc {
+// Internals shared by the solver and the batched engine (solver.cu).
+cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* opt, void* stream,
+                         cluster_ctx* c, bool capture);
+void ctx_free(cluster_ctx* c);
+PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact);
+FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init);
+cluster_status read_state(cluster_ctx* c);
+void fill_report(const cluster_ctx* c, cluster_report* rep);
+int grid_for(int64_t work, int threads);
+}  // namespace fc

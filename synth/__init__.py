@@ -15,10 +15,11 @@ from .gen import (
     dirichlet_u0,
     GraphSpec,
     make_graph,
+    batch_specs,
 )
 
 __all__ = [
     "hash_u64", "uniform01", "stream_key",
     "sbm_pairs", "dcsbm_edges", "two_cluster_er_edges",
-    "assemble_csr", "pair_weights", "dirichlet_u0", "GraphSpec", "make_graph",
+    "assemble_csr", "pair_weights", "dirichlet_u0", "GraphSpec", "make_graph", "batch_specs",
 ]

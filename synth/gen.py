@@ -324,3 +324,21 @@ def make_graph(spec: GraphSpec, device=None):
         raise ValueError(f"unknown graph kind {spec.kind}")
     return assemble_csr(spec.n, s, d, spec.seed)
 
+
+def batch_specs(count: int, seed: int = 3, n_range=(500, 200_000), ks=(4, 8, 16, 32, 64),
+                deg_range=(10.0, 40.0)) -> list:
+    """Instances of a batched workload: n log-uniform in n_range, k uniform
+    over ks, mean degree uniform in deg_range, DC-SBM graphs with B = k blocks
+    and seed + b per instance (draws from the same counter-based generator)."""
+    idx = torch.arange(count, dtype=torch.int64)
+    un = uniform01(seed, 101, idx).numpy()
+    uk = below(seed, 102, idx, len(ks)).numpy()
+    ud = uniform01(seed, 103, idx).numpy()
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    out = []
+    for b in range(count):
+        n = int(round(math.exp(lo + (hi - lo) * (1.0 - un[b]))))
+        k = int(ks[int(uk[b])])
+        d = deg_range[0] + (deg_range[1] - deg_range[0]) * (1.0 - ud[b])
+        out.append(GraphSpec("dcsbm", n, k, seed + b, mean_deg=d))
+    return out
