@@ -269,6 +269,17 @@ CLUSTER_API cluster_status cluster_batch_enqueue(cluster_batch* b, int64_t iters
  * (may be NULL). */
 CLUSTER_API cluster_status cluster_batch_step(cluster_batch* b, int64_t iters, cluster_report* reps);
 
+/* Choose the launch shapes (resident blocks per SM) of the batch's two
+ * persistent kernels per class by timing candidates on live iterations:
+ * each trial advances every unfinished instance by one iteration, exactly as
+ * cluster_batch_step would (a launch shape changes no value).  About
+ * trials x (sum over classes of the candidate count) iterations are used;
+ * the CUDA graph is re-captured with the chosen shapes. */
+CLUSTER_API cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trials);
+
+/* JSON description of the batch's classes and launch shapes into buf. */
+CLUSTER_API cluster_status cluster_batch_describe(cluster_batch* b, char* buf, size_t len);
+
 /* Copy instance i's output iterate into U_out (device, n_i x k_i). */
 CLUSTER_API cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, float* U_out);
 

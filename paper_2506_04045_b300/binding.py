@@ -89,6 +89,8 @@ _SIGS = {
     "cluster_batch_enqueue": (ctypes.c_int, [_P, ctypes.c_int64]),
     "cluster_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(Report)]),
     "cluster_batch_get_U": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cluster_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cluster_batch_describe": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "cluster_batch_destroy": (None, [_P]),
     "cluster_csr_from_edges": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
                                               ctypes.POINTER(CSR)]),
@@ -278,6 +280,16 @@ class Batch:
 
     def enqueue(self, iters: int) -> None:
         check(self._lib.cluster_batch_enqueue(self._ctx, int(iters)))
+
+    def autotune(self, trials: int = 1) -> dict:
+        check(self._lib.cluster_batch_autotune(self._ctx, int(trials)))
+        return self.describe()
+
+    def describe(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        check(self._lib.cluster_batch_describe(self._ctx, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def get_U(self, i: int, out=None):
         import torch

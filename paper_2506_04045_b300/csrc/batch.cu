@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "batch_kernels.cuh"
@@ -37,6 +38,9 @@ struct BatchClass {
   int n_items = 0;
   int64_t units = 0, heavy = 0;
   int spmm_grid = 1, upd_grid = 1, fin_grid = 1;
+  int occ_spmm = 1, occ_upd = 1;   // resident blocks per SM of the two persistent kernels
+  int64_t gather_blocks_max = 1;   // blocks beyond this would find no gather unit
+  bool tuned = false;
   BatchMeta meta{};
 };
 
@@ -59,9 +63,11 @@ struct BOps {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, false>, L::NT, 0);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_update_kernel<KP, false>, L::NT, smem);
     }
+    bc.occ_spmm = std::max(1, o1);
+    bc.occ_upd = std::max(1, o2);
     bc.spmm_grid = sms * std::max(1, o1);
-    const int64_t warps_needed = (bc.units + L::WARPS - 1) / L::WARPS;
-    bc.spmm_grid = (int)std::max<int64_t>(1, std::min<int64_t>(bc.spmm_grid, warps_needed));
+    bc.gather_blocks_max = std::max<int64_t>(1, (bc.units + L::WARPS - 1) / L::WARPS);
+    bc.spmm_grid = (int)std::min<int64_t>(bc.spmm_grid, bc.gather_blocks_max);
     bc.upd_grid = std::max(1, std::min(sms * std::max(1, o2), bc.n_items));
     const int64_t fin_threads = bc.heavy * L::T;
     bc.fin_grid = (int)std::max<int64_t>(1, std::min<int64_t>((fin_threads + 255) / 256, 4096));
@@ -77,6 +83,21 @@ struct BOps {
     batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
   }
   static int64_t units(const cluster_ctx* c) { return spmm_units<KP>(c->n, c->n_heavy, c->n_chunks); }
+  // one iteration with events around the two persistent kernels
+  static void timed_iteration(const BatchClass& bc, int spmm_grid, int upd_grid, cudaEvent_t* ev, cudaStream_t s) {
+    cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
+    const size_t smem = pass_smem_bytes<KP>(false);
+    cudaEventRecord(ev[0], s);
+    if (bc.mixed) batch_spmm_kernel<KP, true><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
+    else batch_spmm_kernel<KP, false><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
+    cudaEventRecord(ev[1], s);
+    if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
+    cudaEventRecord(ev[2], s);
+    if (bc.mixed) batch_update_kernel<KP, true><<<upd_grid, L::NT, smem, s>>>(bc.meta);
+    else batch_update_kernel<KP, false><<<upd_grid, L::NT, smem, s>>>(bc.meta);
+    cudaEventRecord(ev[3], s);
+    batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
+  }
 };
 
 #define FC_BDISPATCH(KPV, CALL)                      \
@@ -104,12 +125,16 @@ struct cluster_batch {
   std::vector<FistaState> h_collect;
   int graph_chunk = 16;
   cudaGraphExec_t graph = nullptr;
+  std::vector<cudaStream_t> branch;  // one capture stream per class
+  std::vector<cudaEvent_t> ev;       // fork event + one join event per class
 };
 
 static void batch_free(cluster_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   for (auto& bc : b->classes) {
     void* ps[] = {bc.d_args, bc.d_folds, bc.d_unit_base, bc.d_heavy_base, bc.d_item_inst, bc.d_item_slot,
                   bc.d_parts, bc.d_states, bc.d_work};
@@ -186,8 +211,40 @@ static cluster_status build_class(cluster_batch* b, BatchClass& bc, int sms) {
   return CLUSTER_OK;
 }
 
-static void batch_iteration(const cluster_batch* b, cudaStream_t s) {
-  for (const BatchClass& bc : b->classes) FC_BDISPATCH(bc.KP, Ops::iteration(bc, s));
+// Graph of graph_chunk iterations of every class.  Classes share no data, so
+// each class's chain of iterations is its own branch of the graph (fork at
+// the start, join at the end) and the classes' kernels overlap on the GPU.
+static cluster_status capture_batch_graph(cluster_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const size_t ncls = b->classes.size();
+  while (b->branch.size() < ncls) {
+    cudaStream_t st = nullptr;
+    FC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->branch.push_back(st);
+  }
+  while (b->ev.size() < ncls + 1) {
+    cudaEvent_t e = nullptr;
+    FC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->ev.push_back(e);
+  }
+  cudaGraph_t g = nullptr;
+  FC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  FC_CUDA(cudaEventRecord(b->ev[0], b->cap_stream));
+  for (size_t ci = 0; ci < ncls; ++ci) {
+    const BatchClass& bc = b->classes[ci];
+    FC_CUDA(cudaStreamWaitEvent(b->branch[ci], b->ev[0], 0));
+    for (int i = 0; i < b->graph_chunk; ++i) FC_BDISPATCH(bc.KP, Ops::iteration(bc, b->branch[ci]));
+    FC_CUDA(cudaEventRecord(b->ev[ci + 1], b->branch[ci]));
+    FC_CUDA(cudaStreamWaitEvent(b->cap_stream, b->ev[ci + 1], 0));
+  }
+  FC_CUDA(cudaStreamEndCapture(b->cap_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  FC_CUDA(e);
+  return CLUSTER_OK;
 }
 
 static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const cluster_csr* S, const int32_t* k,
@@ -238,15 +295,7 @@ static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const c
   FC_CUDA(cudaMalloc(&b->d_collect, sizeof(FistaState) * count));
   b->h_collect.resize(count);
   FC_CUDA(cudaStreamSynchronize(b->stream));
-  // graph of graph_chunk iterations of every class
-  cudaGraph_t g = nullptr;
-  FC_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < b->graph_chunk; ++i) batch_iteration(b, b->cap_stream);
-  FC_CUDA(cudaStreamEndCapture(b->cap_stream, &g));
-  cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
-  cudaGraphDestroy(g);
-  FC_CUDA(e);
-  return CLUSTER_OK;
+  return capture_batch_graph(b);
 }
 
 extern "C" cluster_status cluster_batch_create(int32_t count, const cluster_csr* S, const int32_t* k,
@@ -308,6 +357,124 @@ extern "C" cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, float
   if (!b || !U_out) FC_EINVAL("NULL argument");
   if (i < 0 || i >= (int32_t)b->inst.size()) FC_EINVAL("instance index %d out of range", i);
   return cluster_get_U(b->inst[i], U_out);
+}
+
+// Launch shapes of the two persistent kernels per class, chosen by timing.
+// Candidates: 1..occupancy resident blocks per SM for the gather kernel, then
+// for the update kernel (with the best gather shape).  Every trial is a real
+// iteration of all unfinished instances; a launch shape changes no value
+// (work units and update items are fixed per instance), so tuning does not
+// perturb the solve.  The graph is re-captured with the chosen shapes.
+extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trials) {
+  clear_error();
+  if (!b) FC_EINVAL("batch is NULL");
+  if (trials < 1) trials = 1;
+  FC_CUDA(cudaSetDevice(b->dev));
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
+  const int m = (int)b->inst.size();
+  const int ncls = (int)b->classes.size();
+  int max_cand = 1;
+  for (auto& bc : b->classes) max_cand = std::max(max_cand, bc.occ_spmm + bc.occ_upd);
+  std::vector<std::vector<double>> t_spmm(ncls), t_upd(ncls);
+  std::vector<cudaEvent_t> ev((size_t)ncls * 4);
+  for (auto& e : ev) FC_CUDA(cudaEventCreate(&e));
+  std::vector<int> best_s(ncls), best_u(ncls);
+  for (int ci = 0; ci < ncls; ++ci) {
+    best_s[ci] = b->classes[ci].spmm_grid;
+    best_u[ci] = b->classes[ci].upd_grid;
+  }
+  cluster_status st = CLUSTER_OK;
+  for (int cand = 0; cand < max_cand && st == CLUSTER_OK; ++cand) {
+    for (int rep = 0; rep < trials && st == CLUSTER_OK; ++rep) {
+      batch_set_limit_kernel<<<(m + 255) / 256, 256, 0, b->stream>>>(b->d_all_states, m, 1);
+      std::vector<int> gs(ncls), gu(ncls);
+      for (int ci = 0; ci < ncls; ++ci) {
+        BatchClass& bc = b->classes[ci];
+        if (cand < bc.occ_spmm) {
+          gs[ci] = (int)std::min<int64_t>((int64_t)sms * (cand + 1), bc.gather_blocks_max);
+          gu[ci] = bc.upd_grid;
+        } else {
+          const int cu = cand - bc.occ_spmm;
+          gs[ci] = best_s[ci];
+          gu[ci] = std::max(1, std::min(sms * (std::min(cu, bc.occ_upd - 1) + 1), bc.n_items));
+        }
+        FC_BDISPATCH(bc.KP, Ops::timed_iteration(bc, gs[ci], gu[ci], &ev[(size_t)ci * 4], b->stream));
+      }
+      cudaError_t e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) {
+        set_error("autotune: %s", cudaGetErrorString(e));
+        st = CLUSTER_ECUDA;
+        break;
+      }
+      for (int ci = 0; ci < ncls; ++ci) {
+        BatchClass& bc = b->classes[ci];
+        float ms_s = 0.f, ms_u = 0.f;
+        cudaEventElapsedTime(&ms_s, ev[(size_t)ci * 4 + 0], ev[(size_t)ci * 4 + 1]);
+        cudaEventElapsedTime(&ms_u, ev[(size_t)ci * 4 + 2], ev[(size_t)ci * 4 + 3]);
+        if (cand < bc.occ_spmm) {
+          t_spmm[ci].push_back(ms_s);
+          if (rep == trials - 1) {
+            // best over the candidates timed so far (min over its trials)
+            const size_t nc = t_spmm[ci].size() / trials;
+            double best = 1e30;
+            for (size_t c2 = 0; c2 < nc; ++c2) {
+              double mn = 1e30;
+              for (int r = 0; r < trials; ++r) mn = std::min(mn, t_spmm[ci][c2 * trials + r]);
+              if (mn < best) {
+                best = mn;
+                best_s[ci] = (int)std::min<int64_t>((int64_t)sms * (c2 + 1), bc.gather_blocks_max);
+              }
+            }
+          }
+        } else if (cand - bc.occ_spmm < bc.occ_upd) {
+          t_upd[ci].push_back(ms_u);
+          if (rep == trials - 1) {
+            const size_t nc = t_upd[ci].size() / trials;
+            double best = 1e30;
+            for (size_t c2 = 0; c2 < nc; ++c2) {
+              double mn = 1e30;
+              for (int r = 0; r < trials; ++r) mn = std::min(mn, t_upd[ci][c2 * trials + r]);
+              if (mn < best) {
+                best = mn;
+                best_u[ci] = std::max(1, std::min(sms * ((int)c2 + 1), bc.n_items));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != CLUSTER_OK) return st;
+  for (int ci = 0; ci < ncls; ++ci) {
+    b->classes[ci].spmm_grid = best_s[ci];
+    b->classes[ci].upd_grid = best_u[ci];
+    b->classes[ci].tuned = true;
+  }
+  FC_TRY(capture_batch_graph(b));
+  return batch_read(b, nullptr);
+}
+
+// Classes and launch shapes as JSON (for reports).
+extern "C" cluster_status cluster_batch_describe(cluster_batch* b, char* buf, size_t len) {
+  clear_error();
+  if (!b || !buf || len == 0) FC_EINVAL("NULL argument");
+  std::string out = "{\"instances\": " + std::to_string(b->inst.size()) + ", \"classes\": [";
+  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+    const BatchClass& bc = b->classes[ci];
+    char tmp[512];
+    snprintf(tmp, sizeof(tmp),
+             "%s{\"kp\": %d, \"mixed\": %d, \"instances\": %zu, \"gather_units\": %lld, \"chunked_rows\": %lld, "
+             "\"update_items\": %d, \"gather_blocks\": %d, \"update_blocks\": %d, \"tuned\": %d}",
+             ci ? ", " : "", bc.KP, bc.mixed ? 1 : 0, bc.members.size(), (long long)bc.units, (long long)bc.heavy,
+             bc.n_items, bc.spmm_grid, bc.upd_grid, bc.tuned ? 1 : 0);
+    out += tmp;
+  }
+  out += "]}";
+  if (out.size() + 1 > len) FC_EINVAL("buffer too small (%zu bytes needed)", out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return CLUSTER_OK;
 }
 
 extern "C" void cluster_batch_destroy(cluster_batch* b) {

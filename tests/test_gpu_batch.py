@@ -61,6 +61,23 @@ def test_batch_equals_solo_bitwise(precision):
     b.close()
 
 
+def test_autotuned_batch_still_equals_solo():
+    inst = _instances(MIXED_SPECS[:7])
+    opts = dict(stop_rule=pkg.STOP_NONE, max_iter=60)
+    b = pkg.Batch(inst, **opts)
+    desc = b.autotune(trials=1)
+    assert all(c["tuned"] == 1 for c in desc["classes"])
+    done = b.step(0)[0]["iters"]
+    assert 0 < done < 40
+    b.step(40 - done)
+    for i, (rp, c, v, U0) in enumerate(inst):
+        s = pkg.Solver(rp, c, v, U0, **opts)
+        s.step(40)
+        assert torch.equal(b.get_U(i), s.get_U()), i
+        s.close()
+    b.close()
+
+
 def test_batch_against_oracle():
     specs = [MIXED_SPECS[2], MIXED_SPECS[5]]
     inst = _instances(specs)
