@@ -286,6 +286,70 @@ CLUSTER_API cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, floa
 CLUSTER_API void cluster_batch_destroy(cluster_batch* b);
 
 /* ------------------------------------------------------------------------ */
+/* Serving with continuous batching                                          */
+/* ------------------------------------------------------------------------ */
+/* A server owns a worker thread and the current device (at create time).
+ * cluster_server_submit copies a request (host CSR, k, host start point) and
+ * queues it; the worker admits queued requests in arrival order while their
+ * estimated device footprint fits hbm_budget (and max_resident, if set),
+ * keeps admitted solves resident, and advances all of them together
+ * iters_per_tick iterations per tick through the batched launches.  Solves
+ * that stop (their rule or max_iter) are finalised, copied to the host and
+ * freed after the tick in which they stop, which admits more requests.  A
+ * solve's result does not depend on what else is resident: it equals the same
+ * request solved alone with the same options. */
+typedef struct cluster_server cluster_server;
+
+typedef struct cluster_server_options {
+  cluster_options solve;   /* applied to every request (borrow and fused_pass
+                              are set by the server); default stop rule PG_REL,
+                              tol 1e-5, max_iter 5000                          */
+  size_t hbm_budget;       /* device bytes resident solves may use; 0 = 80% of
+                              the free device memory at create time            */
+  int32_t iters_per_tick;  /* default 16                                        */
+  int32_t max_resident;    /* 0 = no limit besides the budget                   */
+} cluster_server_options;
+
+typedef struct cluster_server_stats {
+  uint64_t submitted, admitted, completed, failed, ticks;
+  int64_t queued, resident;
+  size_t resident_bytes, budget_bytes;
+  double uptime_s;
+} cluster_server_stats;
+
+/* Per-request timing (seconds): queue_s = submit -> admission, run_s =
+ * admission -> result on the host, total_s = submit -> result on the host. */
+typedef struct cluster_request_times {
+  double queue_s, run_s, total_s;
+} cluster_request_times;
+
+CLUSTER_API void cluster_server_options_default(cluster_server_options* opt);
+CLUSTER_API cluster_status cluster_server_create(const cluster_server_options* opt, cluster_server** out);
+
+/* Queue a request.  S: host CSR (int32 or int64 row pointers), U0: host n x k.
+ * The server copies both; the caller's buffers may be reused at once. */
+CLUSTER_API cluster_status cluster_server_submit(cluster_server* s, const cluster_csr* S, int32_t k,
+                                                 const float* U0, uint64_t* ticket);
+
+/* CLUSTER_EAGAIN while pending.  Once finished, returns the solve's status
+ * (CLUSTER_OK, or the error that ended it, with cluster_last_error() set),
+ * fills U_out (host, n x k), rep and times (each may be NULL) and forgets the
+ * ticket. */
+CLUSTER_API cluster_status cluster_server_poll(cluster_server* s, uint64_t ticket, float* U_out,
+                                               cluster_report* rep, cluster_request_times* times);
+
+/* Like poll but blocks up to timeout_s seconds; CLUSTER_ETIMEOUT if still
+ * pending then (the ticket stays valid). */
+CLUSTER_API cluster_status cluster_server_wait(cluster_server* s, uint64_t ticket, double timeout_s,
+                                               float* U_out, cluster_report* rep, cluster_request_times* times);
+
+CLUSTER_API cluster_status cluster_server_get_stats(cluster_server* s, cluster_server_stats* out);
+
+/* Stop the worker after its current tick; unfinished requests end with
+ * CLUSTER_EAGAIN.  Frees everything. */
+CLUSTER_API void cluster_server_destroy(cluster_server* s);
+
+/* ------------------------------------------------------------------------ */
 /* CSR construction (host)                                                   */
 /* ------------------------------------------------------------------------ */
 /* Build the symmetric similarity matrix from an edge list (Example 4.1):

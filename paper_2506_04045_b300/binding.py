@@ -64,6 +64,28 @@ class KernelTimes(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("solve", Options), ("hbm_budget", ctypes.c_size_t), ("iters_per_tick", ctypes.c_int32),
+                ("max_resident", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("ticks", ctypes.c_uint64), ("queued", ctypes.c_int64),
+                ("resident", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("uptime_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("total_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "cluster_options_default": (None, [ctypes.POINTER(Options)]),
@@ -92,6 +114,16 @@ _SIGS = {
     "cluster_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cluster_batch_describe": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "cluster_batch_destroy": (None, [_P]),
+    "cluster_server_options_default": (None, [ctypes.POINTER(ServerOptions)]),
+    "cluster_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(_P)]),
+    "cluster_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(CSR), ctypes.c_int32, _P,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+    "cluster_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(Report),
+                                           ctypes.POINTER(RequestTimes)]),
+    "cluster_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, _P, ctypes.POINTER(Report),
+                                           ctypes.POINTER(RequestTimes)]),
+    "cluster_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "cluster_server_destroy": (None, [_P]),
     "cluster_csr_from_edges": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
                                               ctypes.POINTER(CSR)]),
     "cluster_csr_free": (None, [ctypes.POINTER(CSR)]),
@@ -302,6 +334,87 @@ class Batch:
     def close(self) -> None:
         if self._ctx:
             self._lib.cluster_batch_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """cluster_server: continuous-batching solves of host-side requests.
+    Requests are (row_ptr, col, val, U0) numpy arrays (int64/int32, int32,
+    float32, float32 n x k)."""
+
+    def __init__(self, hbm_budget: int = 0, iters_per_tick: int = 16, max_resident: int = 0, **solve_opts):
+        self._lib = load()
+        o = ServerOptions()
+        self._lib.cluster_server_options_default(ctypes.byref(o))
+        o.hbm_budget = int(hbm_budget)
+        o.iters_per_tick = int(iters_per_tick)
+        o.max_resident = int(max_resident)
+        for k, v in solve_opts.items():
+            if not hasattr(o.solve, k):
+                raise KeyError(k)
+            setattr(o.solve, k, v)
+        self.options = o
+        self._ctx = ctypes.c_void_p()
+        self._shapes = {}
+        check(self._lib.cluster_server_create(ctypes.byref(o), ctypes.byref(self._ctx)))
+
+    def submit(self, row_ptr, col, val, U0) -> int:
+        rp = np.ascontiguousarray(row_ptr)
+        if rp.dtype not in (np.int64, np.int32):
+            rp = rp.astype(np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float32)
+        U0 = np.ascontiguousarray(U0, dtype=np.float32)
+        s = CSR()
+        s.n = rp.size - 1
+        s.nnz = col.size
+        s.index64 = 1 if rp.dtype == np.int64 else 0
+        s.row_ptr = rp.ctypes.data
+        s.col = col.ctypes.data if col.size else 0
+        s.val = val.ctypes.data if val.size else 0
+        t = ctypes.c_uint64()
+        check(self._lib.cluster_server_submit(self._ctx, ctypes.byref(s), int(U0.shape[1]), U0.ctypes.data,
+                                              ctypes.byref(t)))
+        self._shapes[t.value] = U0.shape
+        return t.value
+
+    def _result(self, ticket, st, U, rep, times):
+        self._shapes.pop(ticket, None)
+        check(st)
+        return U, rep.as_dict(), times.as_dict()
+
+    def poll(self, ticket: int):
+        """None while pending, else (U, report, times); raises ClusterError if the solve failed."""
+        U = np.empty(self._shapes[ticket], dtype=np.float32)
+        rep, times = Report(), RequestTimes()
+        st = self._lib.cluster_server_poll(self._ctx, ticket, U.ctypes.data, ctypes.byref(rep), ctypes.byref(times))
+        if st == EAGAIN:
+            return None
+        return self._result(ticket, st, U, rep, times)
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        U = np.empty(self._shapes[ticket], dtype=np.float32)
+        rep, times = Report(), RequestTimes()
+        st = self._lib.cluster_server_wait(self._ctx, ticket, float(timeout), U.ctypes.data, ctypes.byref(rep),
+                                           ctypes.byref(times))
+        if st == ETIMEOUT:
+            raise ClusterError(st, last_error())
+        return self._result(ticket, st, U, rep, times)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(self._lib.cluster_server_get_stats(self._ctx, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self._ctx:
+            self._lib.cluster_server_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcluster.so")
-SOURCES = ["solver.cu", "batch.cu", "objective_static.cu", "csr_build.cpp"]
+SOURCES = ["solver.cu", "batch.cu", "server.cu", "objective_static.cu", "csr_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -127,23 +127,34 @@ struct cluster_batch {
   cudaGraphExec_t graph = nullptr;
   std::vector<cudaStream_t> branch;  // one capture stream per class
   std::vector<cudaEvent_t> ev;       // fork event + one join event per class
+  bool owns = true;                  // destroy frees the instances too
 };
 
-static void batch_free(cluster_batch* b) {
-  if (!b) return;
+// Free the per-class tables, state arrays and graph (not the instances).
+static void batch_release_tables(cluster_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
-  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  b->graph = nullptr;
   for (auto& bc : b->classes) {
     void* ps[] = {bc.d_args, bc.d_folds, bc.d_unit_base, bc.d_heavy_base, bc.d_item_inst, bc.d_item_slot,
                   bc.d_parts, bc.d_states, bc.d_work};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
+  b->classes.clear();
   if (b->d_all_states) cudaFree(b->d_all_states);
   if (b->d_collect) cudaFree(b->d_collect);
-  for (cluster_ctx* c : b->inst) ctx_free(c);
+  b->d_all_states = nullptr;
+  b->d_collect = nullptr;
+}
+
+static void batch_free(cluster_batch* b) {
+  if (!b) return;
+  batch_release_tables(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->owns)
+    for (cluster_ctx* c : b->inst) ctx_free(c);
   delete b;
 }
 
@@ -247,33 +258,14 @@ static cluster_status capture_batch_graph(cluster_batch* b) {
   return CLUSTER_OK;
 }
 
-static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const cluster_csr* S, const int32_t* k,
-                                        const float* const* U0, const cluster_options* optp, void* stream) {
-  if (count < 1) FC_EINVAL("count must be >= 1");
-  if (!S || !k || !U0) FC_EINVAL("NULL argument");
-  cluster_options opt;
-  if (optp) opt = *optp;
-  else cluster_options_default(&opt);
-  if (opt.fused_pass) FC_EINVAL("batched solves use the split iteration (fused_pass must be 0)");
-  if (opt.graph_chunk < 1) opt.graph_chunk = 16;
-  b->opt = opt;
-  b->stream = (cudaStream_t)stream;
-  b->graph_chunk = opt.graph_chunk;
-  FC_CUDA(cudaGetDevice(&b->dev));
-  FC_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+// Group b->inst into classes, upload the tables and capture the graph.
+static cluster_status batch_assemble(cluster_batch* b) {
+  batch_release_tables(b);
+  const int count = (int)b->inst.size();
+  if (count == 0) return CLUSTER_OK;
   std::map<std::pair<int, int>, int> cls;
-  for (int32_t i = 0; i < count; ++i) {
-    cluster_ctx* c = new (std::nothrow) cluster_ctx();
-    if (!c) {
-      set_error("out of host memory");
-      return CLUSTER_ENOMEM;
-    }
-    b->inst.push_back(c);
-    cluster_status st = init_impl(&S[i], k[i], U0[i], &opt, stream, c, false);
-    if (st != CLUSTER_OK) {
-      set_error("instance %d: %s", i, cluster_last_error());
-      return st;
-    }
+  for (int i = 0; i < count; ++i) {
+    const cluster_ctx* c = b->inst[i];
     const auto key = std::make_pair(c->KP, c->mixed ? 1 : 0);
     auto it = cls.find(key);
     if (it == cls.end()) {
@@ -296,6 +288,36 @@ static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const c
   b->h_collect.resize(count);
   FC_CUDA(cudaStreamSynchronize(b->stream));
   return capture_batch_graph(b);
+}
+
+static cluster_status batch_create_impl(cluster_batch* b, int32_t count, const cluster_csr* S, const int32_t* k,
+                                        const float* const* U0, const cluster_options* optp, void* stream) {
+  if (count < 1) FC_EINVAL("count must be >= 1");
+  if (!S || !k || !U0) FC_EINVAL("NULL argument");
+  cluster_options opt;
+  if (optp) opt = *optp;
+  else cluster_options_default(&opt);
+  if (opt.fused_pass) FC_EINVAL("batched solves use the split iteration (fused_pass must be 0)");
+  if (opt.graph_chunk < 1) opt.graph_chunk = 16;
+  b->opt = opt;
+  b->stream = (cudaStream_t)stream;
+  b->graph_chunk = opt.graph_chunk;
+  FC_CUDA(cudaGetDevice(&b->dev));
+  FC_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  for (int32_t i = 0; i < count; ++i) {
+    cluster_ctx* c = new (std::nothrow) cluster_ctx();
+    if (!c) {
+      set_error("out of host memory");
+      return CLUSTER_ENOMEM;
+    }
+    b->inst.push_back(c);
+    cluster_status st = init_impl(&S[i], k[i], U0[i], &opt, stream, c, false);
+    if (st != CLUSTER_OK) {
+      set_error("instance %d: %s", i, cluster_last_error());
+      return st;
+    }
+  }
+  return batch_assemble(b);
 }
 
 extern "C" cluster_status cluster_batch_create(int32_t count, const cluster_csr* S, const int32_t* k,
@@ -321,6 +343,7 @@ extern "C" cluster_status cluster_batch_create(int32_t count, const cluster_csr*
 
 static cluster_status batch_read(cluster_batch* b, cluster_report* reps) {
   const int m = (int)b->inst.size();
+  if (m == 0) return CLUSTER_OK;
   batch_collect_kernel<<<m, 64, 0, b->stream>>>(b->d_all_states, m, b->d_collect);
   FC_CUDA(cudaGetLastError());
   FC_CUDA(cudaMemcpyAsync(b->h_collect.data(), b->d_collect, sizeof(FistaState) * m, cudaMemcpyDeviceToHost,
@@ -337,7 +360,7 @@ extern "C" cluster_status cluster_batch_enqueue(cluster_batch* b, int64_t iters)
   clear_error();
   if (!b) FC_EINVAL("batch is NULL");
   if (iters < 0) FC_EINVAL("iters must be >= 0");
-  if (iters == 0) return CLUSTER_OK;
+  if (iters == 0 || b->inst.empty()) return CLUSTER_OK;
   FC_CUDA(cudaSetDevice(b->dev));
   const int m = (int)b->inst.size();
   batch_set_limit_kernel<<<(m + 255) / 256, 256, 0, b->stream>>>(b->d_all_states, m, iters);
@@ -483,3 +506,46 @@ extern "C" void cluster_batch_destroy(cluster_batch* b) {
   cudaStreamSynchronize(b->stream);
   batch_free(b);
 }
+
+// ---------------------------------------------------------------------------
+// non-owning batches over instances owned by someone else (the server)
+// ---------------------------------------------------------------------------
+namespace fc {
+
+cluster_status batch_view_new(void* stream, int graph_chunk, cluster_batch** out) {
+  cluster_batch* b = new (std::nothrow) cluster_batch();
+  if (!b) {
+    set_error("out of host memory");
+    return CLUSTER_ENOMEM;
+  }
+  b->owns = false;
+  b->stream = (cudaStream_t)stream;
+  b->graph_chunk = graph_chunk < 1 ? 16 : graph_chunk;
+  cudaError_t e = cudaGetDevice(&b->dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    set_error("batch view: %s", cudaGetErrorString(e));
+    return CLUSTER_ECUDA;
+  }
+  *out = b;
+  return CLUSTER_OK;
+}
+
+cluster_status batch_view_set(cluster_batch* b, const std::vector<cluster_ctx*>& members) {
+  b->inst = members;
+  return batch_assemble(b);
+}
+
+cluster_status batch_view_run(cluster_batch* b, int64_t iters) {
+  FC_TRY(cluster_batch_enqueue(b, iters));
+  return batch_read(b, nullptr);
+}
+
+void batch_view_delete(cluster_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+}
+
+}  // namespace fc

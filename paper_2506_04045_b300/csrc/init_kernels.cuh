@@ -19,12 +19,12 @@ enum : int {
   kErrU0Sum = 128,     // U0 row sum differs from 1 by more than 1e-5
 };
 
-__global__ void rowptr32_to_64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n1) {
+static __global__ void rowptr32_to_64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n1) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = in[i];
 }
 
-__global__ void validate_rowptr_kernel(const int64_t* __restrict__ rp, int64_t n, int64_t nnz, int* err) {
+static __global__ void validate_rowptr_kernel(const int64_t* __restrict__ rp, int64_t n, int64_t nnz, int* err) {
   int bits = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = rp[i];
@@ -38,7 +38,7 @@ __global__ void validate_rowptr_kernel(const int64_t* __restrict__ rp, int64_t n
 
 // Runs only after validate_rowptr_kernel found row_ptr sound, so every
 // index it forms stays inside [0, nnz).
-__global__ void validate_csr_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+static __global__ void validate_csr_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                     const float* __restrict__ val, int64_t n, int need_diag, int* err) {
   int bits = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -60,7 +60,7 @@ __global__ void validate_csr_kernel(const int64_t* __restrict__ rp, const int32_
 
 // s_ij must equal s_ji: look up (j, i) by binary search in row j (runs only on
 // a structurally valid CSR).
-__global__ void validate_sym_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+static __global__ void validate_sym_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                     const float* __restrict__ val, int64_t n, int* err) {
   int bits = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -78,7 +78,7 @@ __global__ void validate_sym_kernel(const int64_t* __restrict__ rp, const int32_
   if (bits) atomicOr(err, bits);
 }
 
-__global__ void validate_u0_kernel(const float* __restrict__ U, int64_t n, int k, int* err) {
+static __global__ void validate_u0_kernel(const float* __restrict__ U, int64_t n, int k, int* err) {
   int bits = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -93,7 +93,7 @@ __global__ void validate_u0_kernel(const float* __restrict__ U, int64_t n, int k
 }
 
 // Per-block float64 partial sums of val^2 (folded on the host in block order).
-__global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ val, int64_t nnz,
+static __global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ val, int64_t nnz,
                                                      double* __restrict__ part) {
   __shared__ double red[256];
   double s = 0.0;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ va
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void degree_kernel(const int64_t* __restrict__ rp, int64_t n, uint32_t* __restrict__ deg,
+static __global__ void degree_kernel(const int64_t* __restrict__ rp, int64_t n, uint32_t* __restrict__ deg,
                               int32_t* __restrict__ iota) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = rp[i + 1] - rp[i];
@@ -119,7 +119,7 @@ __global__ void degree_kernel(const int64_t* __restrict__ rp, int64_t n, uint32_
   }
 }
 
-__global__ void count_above_kernel(const uint32_t* __restrict__ deg, int64_t n, uint32_t thr,
+static __global__ void count_above_kernel(const uint32_t* __restrict__ deg, int64_t n, uint32_t thr,
                                    unsigned long long* cnt) {
   unsigned long long c = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -127,7 +127,7 @@ __global__ void count_above_kernel(const uint32_t* __restrict__ deg, int64_t n, 
   if (c) atomicAdd(cnt, c);
 }
 
-__global__ void heavy_lo_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ order, int64_t nh,
+static __global__ void heavy_lo_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ order, int64_t nh,
                                 int64_t* __restrict__ lo) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nh; p += (int64_t)gridDim.x * blockDim.x)
     lo[p] = rp[order[p]];
@@ -135,7 +135,7 @@ __global__ void heavy_lo_kernel(const int64_t* __restrict__ rp, const int32_t* _
 
 // cost of a position: chunk count for chunked rows, degree otherwise, plus a
 // fixed per-row charge for the row-local traffic and the epilogue
-__global__ void cost_kernel(const uint32_t* __restrict__ sdeg, int64_t n, int64_t nh, uint32_t chunk,
+static __global__ void cost_kernel(const uint32_t* __restrict__ sdeg, int64_t n, int64_t nh, uint32_t chunk,
                             int64_t row_cost, int64_t* __restrict__ cost) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = sdeg[p];
@@ -144,7 +144,7 @@ __global__ void cost_kernel(const uint32_t* __restrict__ sdeg, int64_t n, int64_
 }
 
 // cta_pos[c] = first position whose inclusive cost prefix exceeds c * total / parts
-__global__ void partition_kernel(const int64_t* __restrict__ prefix, int64_t n, int parts,
+static __global__ void partition_kernel(const int64_t* __restrict__ prefix, int64_t n, int parts,
                                  int64_t* __restrict__ cta_pos) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c > parts) return;
@@ -168,7 +168,7 @@ __global__ void partition_kernel(const int64_t* __restrict__ prefix, int64_t n, 
 }
 
 // n x k (row-major, stride k) -> n x KP zero-padded float32 (+ optional copies)
-__global__ void pad_kernel(const float* __restrict__ U, int64_t n, int k, int KP, float* __restrict__ X,
+static __global__ void pad_kernel(const float* __restrict__ U, int64_t n, int k, int KP, float* __restrict__ X,
                            float* __restrict__ X2, __nv_bfloat16* __restrict__ XS,
                            __nv_bfloat16* __restrict__ XS2) {
   const int64_t tot = n * KP;
@@ -183,7 +183,7 @@ __global__ void pad_kernel(const float* __restrict__ U, int64_t n, int k, int KP
   }
 }
 
-__global__ void unpad_kernel(const float* __restrict__ X, int64_t n, int k, int KP, float* __restrict__ U) {
+static __global__ void unpad_kernel(const float* __restrict__ X, int64_t n, int k, int KP, float* __restrict__ U) {
   const int64_t tot = n * k;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / k;
@@ -192,13 +192,13 @@ __global__ void unpad_kernel(const float* __restrict__ X, int64_t n, int k, int 
   }
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ in, int64_t m, __nv_bfloat16* __restrict__ out) {
+static __global__ void to_bf16_kernel(const float* __restrict__ in, int64_t m, __nv_bfloat16* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = __float2bfloat16_rn(in[i]);
 }
 
 // y = S x, one thread per row (set-up only)
-__global__ void spmv_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+static __global__ void spmv_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const float* __restrict__ val, const double* __restrict__ x, int64_t n,
                             double* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -208,7 +208,7 @@ __global__ void spmv_kernel(const int64_t* __restrict__ rp, const int32_t* __res
   }
 }
 
-__global__ void __launch_bounds__(256) dot_part_kernel(const double* __restrict__ a, const double* __restrict__ b,
+static __global__ void __launch_bounds__(256) dot_part_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                                         int64_t n, double* __restrict__ part) {
   __shared__ double red[256];
   double s = 0.0;
@@ -223,12 +223,12 @@ __global__ void __launch_bounds__(256) dot_part_kernel(const double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void scale_kernel(double* __restrict__ x, int64_t n, double s) {
+static __global__ void scale_kernel(double* __restrict__ x, int64_t n, double s) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= s;
 }
 
-__global__ void fill_start_kernel(double* __restrict__ x, int64_t n) {
+static __global__ void fill_start_kernel(double* __restrict__ x, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     // fixed, strictly positive start vector (not orthogonal to the Perron vector of a nonnegative S)
     uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull;

@@ -687,7 +687,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   return CLUSTER_OK;
 }
 
-static cluster_status finalize_loss(cluster_ctx* c) {
+cluster_status finalize_loss(cluster_ctx* c) {
   FistaState& h = c->host_st;
   if (h.f_iter == h.out_iter || h.status == 4) return CLUSTER_OK;
   enqueue_eval(c, (int)(h.out_iter & 1), 0, c->stream);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/cluster.h"
 #include "pass_kernels.cuh"
 #include "state.h"
@@ -65,5 +67,12 @@ PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact);
 FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init);
 cluster_status read_state(cluster_ctx* c);
 void fill_report(const cluster_ctx* c, cluster_report* rep);
+cluster_status finalize_loss(cluster_ctx* c);  // make the report's f the loss of the output iterate
 int grid_for(int64_t work, int threads);
+
+// Non-owning batch over instances owned by the caller (batch.cu).
+cluster_status batch_view_new(void* stream, int graph_chunk, cluster_batch** out);
+cluster_status batch_view_set(cluster_batch* b, const std::vector<cluster_ctx*>& members);
+cluster_status batch_view_run(cluster_batch* b, int64_t iters);  // advance and read every member's state
+void batch_view_delete(cluster_batch* b);
 }  // namespace fc
