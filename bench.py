@@ -44,8 +44,17 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--workload", default="paper", choices=["paper", "batch"],
-                   help="paper: one n=70M k=32 instance (default); batch: 512 uneven instances")
+    p.add_argument("--workload", default="paper", choices=["paper", "batch", "serve"],
+                   help="paper: one n=70M k=32 instance (default); batch: 512 uneven instances; "
+                        "serve: Poisson stream of solves through the continuous-batching server")
+    p.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
+    p.add_argument("--drain", type=float, default=30.0, help="serve: seconds to wait for completions afterwards")
+    p.add_argument("--pool", type=int, default=32, help="serve: distinct request graphs drawn from")
+    p.add_argument("--budget-gb", type=float, default=120.0)
+    p.add_argument("--serve-max-iter", type=int, default=5000)
+    p.add_argument("--serve-tol", type=float, default=1e-5)
+    p.add_argument("--tick", type=int, default=16)
     p.add_argument("--instances", type=int, default=512)
     p.add_argument("--n", type=int, default=70_000_000)
     p.add_argument("--k", type=int, default=32)
@@ -515,6 +524,106 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, ws, rank, local):
+    """Serving workload: Poisson arrivals (rate --rate) of solves with n
+    log-uniform in [1e3, 2e6], k in {8, 16, 32, 64, 128}, mean degree U[10, 40],
+    each run to PG_REL --serve-tol (cap --serve-max-iter), admitted under a
+    --budget-gb device budget.  Requests are drawn from a pool of --pool
+    pre-generated graphs (host arrays).  Reports latency percentiles of the
+    requests that finished, and offered vs achieved load; requests still
+    pending at the end are counted, not dropped."""
+    import random
+    import threading
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2506_04045_b300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    specs = synth.batch_specs(args.pool, seed=4 + 1000 * rank, n_range=(1_000, 2_000_000),
+                              ks=(8, 16, 32, 64, 128))
+    pool = []
+    for sp in specs:
+        rp, c, v = synth.make_graph(sp, device="cuda")
+        U0 = synth.dirichlet_u0(sp.n, sp.k, sp.seed, device="cuda")
+        pool.append((rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), U0.cpu().numpy()))
+        del rp, c, v, U0
+    torch.cuda.empty_cache()
+    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, stop_rule=pkg.STOP_PG_REL,
+                     tol=args.serve_tol, max_iter=args.serve_max_iter, borrow_host=True)
+    rng = random.Random(4 + rank)
+    tickets, submit_t = [], {}
+    depth = []
+    stop_sampling = threading.Event()
+
+    def sampler():
+        t0 = time.perf_counter()
+        while not stop_sampling.is_set():
+            st = srv.stats()
+            depth.append((round(time.perf_counter() - t0, 2), st["queued"], st["resident"], st["completed"]))
+            stop_sampling.wait(1.0)
+
+    th = threading.Thread(target=sampler, daemon=True)
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        th.start()
+        t_start = time.perf_counter()
+        t_next = t_start
+        while True:
+            t_next += rng.expovariate(args.rate)
+            if t_next - t_start > args.duration:
+                break
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            req = pool[rng.randrange(len(pool))]
+            tk = srv.submit(*req)
+            tickets.append(tk)
+            submit_t[tk] = time.perf_counter()
+        t_arrivals_end = time.perf_counter()
+        results = {}
+        deadline = t_arrivals_end + args.drain
+        while time.perf_counter() < deadline and len(results) < len(tickets):
+            for tk in tickets:
+                if tk in results:
+                    continue
+                try:
+                    out = srv.poll(tk)
+                except pkg.ClusterError as exc:
+                    results[tk] = ("error", str(exc))
+                    continue
+                if out is not None:
+                    results[tk] = ("ok", out[2], out[1])
+            time.sleep(0.05)
+        t_end = time.perf_counter()
+        stop_sampling.set()
+        th.join(timeout=5)
+    st = srv.stats()
+    srv.close()
+    ok = [r for r in results.values() if r[0] == "ok"]
+    lat = np.array([r[1]["total_s"] for r in ok]) if ok else np.array([])
+    pending = len(tickets) - len(results)
+    span = t_end - t_start
+    line = {"metric": "serving p99 latency (continuous batching)", "value": float(np.percentile(lat, 99)) if ok else None,
+            "unit": "s", "n_gpus": ws, "steps": len(tickets), "warmup": 0, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rate}/s for {args.duration}s, n log-uniform [1e3, 2e6], "
+                                   f"k in {{8..128}}, mean degree U[10,40], PG_REL {args.serve_tol}, "
+                                   f"max_iter {args.serve_max_iter}, budget {args.budget_gb} GB, pool {args.pool}",
+                       "tick": args.tick},
+            "p50_s": float(np.percentile(lat, 50)) if ok else None,
+            "p99_s": float(np.percentile(lat, 99)) if ok else None,
+            "completed": len(ok), "failed": len(results) - len(ok), "pending_at_end": pending,
+            "offered_rps": len(tickets) / args.duration, "achieved_solves_per_s": len(ok) / span,
+            "mean_queue_s": float(np.mean([r[1]["queue_s"] for r in ok])) if ok else None,
+            "mean_run_s": float(np.mean([r[1]["run_s"] for r in ok])) if ok else None,
+            "iterations_of_completed": [int(r[2]["iters"]) for r in ok][:50],
+            "queue_depth": depth[::max(1, len(depth) // 40)], "server_stats": st, "clocks": cs.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -523,6 +632,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, ws, rank, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, ws, rank, local)
         return
     run_native(args, ws, rank, local)
 

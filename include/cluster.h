@@ -308,12 +308,20 @@ typedef struct cluster_server_options {
                               the free device memory at create time            */
   int32_t iters_per_tick;  /* default 16                                        */
   int32_t max_resident;    /* 0 = no limit besides the budget                   */
+  int32_t borrow_host;     /* 1 = submit keeps pointers to the caller's host
+                              arrays instead of copying them; they must stay
+                              valid until the request's result is taken      */
+  int32_t _pad;
+  size_t queue_bytes_max;  /* host bytes of copied, not yet admitted requests
+                              above which submit refuses with CLUSTER_EAGAIN
+                              ("queue full"); an empty queue always accepts
+                              one request; 0 = no limit                       */
 } cluster_server_options;
 
 typedef struct cluster_server_stats {
-  uint64_t submitted, admitted, completed, failed, ticks;
+  uint64_t submitted, admitted, completed, failed, ticks, rejected;
   int64_t queued, resident;
-  size_t resident_bytes, budget_bytes;
+  size_t resident_bytes, budget_bytes, queued_host_bytes;
   double uptime_s;
 } cluster_server_stats;
 
@@ -327,7 +335,8 @@ CLUSTER_API void cluster_server_options_default(cluster_server_options* opt);
 CLUSTER_API cluster_status cluster_server_create(const cluster_server_options* opt, cluster_server** out);
 
 /* Queue a request.  S: host CSR (int32 or int64 row pointers), U0: host n x k.
- * The server copies both; the caller's buffers may be reused at once. */
+ * The server copies both (the caller's buffers may be reused at once) unless
+ * borrow_host is set.  CLUSTER_EAGAIN if the copied-request queue is full. */
 CLUSTER_API cluster_status cluster_server_submit(cluster_server* s, const cluster_csr* S, int32_t k,
                                                  const float* U0, uint64_t* ticket);
 

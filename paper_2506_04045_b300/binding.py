@@ -66,14 +66,15 @@ class KernelTimes(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("solve", Options), ("hbm_budget", ctypes.c_size_t), ("iters_per_tick", ctypes.c_int32),
-                ("max_resident", ctypes.c_int32)]
+                ("max_resident", ctypes.c_int32), ("borrow_host", ctypes.c_int32), ("_pad", ctypes.c_int32),
+                ("queue_bytes_max", ctypes.c_size_t)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
-                ("failed", ctypes.c_uint64), ("ticks", ctypes.c_uint64), ("queued", ctypes.c_int64),
-                ("resident", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
-                ("uptime_s", ctypes.c_double)]
+                ("failed", ctypes.c_uint64), ("ticks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("queued_host_bytes", ctypes.c_size_t), ("uptime_s", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -348,13 +349,17 @@ class Server:
     Requests are (row_ptr, col, val, U0) numpy arrays (int64/int32, int32,
     float32, float32 n x k)."""
 
-    def __init__(self, hbm_budget: int = 0, iters_per_tick: int = 16, max_resident: int = 0, **solve_opts):
+    def __init__(self, hbm_budget: int = 0, iters_per_tick: int = 16, max_resident: int = 0, borrow_host: bool = False,
+                 queue_bytes_max: int = 0, **solve_opts):
         self._lib = load()
         o = ServerOptions()
         self._lib.cluster_server_options_default(ctypes.byref(o))
         o.hbm_budget = int(hbm_budget)
         o.iters_per_tick = int(iters_per_tick)
         o.max_resident = int(max_resident)
+        o.borrow_host = 1 if borrow_host else 0
+        o.queue_bytes_max = int(queue_bytes_max)
+        self._borrowed = {}
         for k, v in solve_opts.items():
             if not hasattr(o.solve, k):
                 raise KeyError(k)
@@ -382,10 +387,13 @@ class Server:
         check(self._lib.cluster_server_submit(self._ctx, ctypes.byref(s), int(U0.shape[1]), U0.ctypes.data,
                                               ctypes.byref(t)))
         self._shapes[t.value] = U0.shape
+        if self.options.borrow_host:
+            self._borrowed[t.value] = (rp, col, val, U0)   # must outlive the request
         return t.value
 
     def _result(self, ticket, st, U, rep, times):
         self._shapes.pop(ticket, None)
+        self._borrowed.pop(ticket, None)
         check(st)
         return U, rep.as_dict(), times.as_dict()
 

@@ -41,10 +41,18 @@ struct Request {
   uint64_t ticket = 0;
   int64_t n = 0, nnz = 0;
   int32_t k = 0;
+  // inputs: owned copies, or the caller's arrays (borrow_host)
   std::vector<int64_t> rp;
   std::vector<int32_t> col;
   std::vector<float> val;
   std::vector<float> U0;
+  const void* b_rp = nullptr;
+  int32_t b_index64 = 1;
+  const int32_t* b_col = nullptr;
+  const float* b_val = nullptr;
+  const float* b_U0 = nullptr;
+  bool borrowed = false;
+  size_t host_bytes = 0;
   size_t footprint = 0;
   // device resources while resident
   int64_t* d_rp = nullptr;
@@ -80,6 +88,7 @@ struct cluster_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   size_t used = 0;
+  size_t queued_host = 0;
   cluster_server_stats stats{};
   double busy_t0 = 0;
 };
@@ -127,17 +136,31 @@ static void release_device(Request* r) {
 
 // Upload and initialise one admitted request on the worker's stream.
 static cluster_status admit(cluster_server* sv, Request* r, cudaStream_t s) {
+  if (r->borrowed) {
+    // row pointers are uploaded as int64; widen an int32 array first
+    if (r->b_index64) {
+      r->rp.clear();
+    } else {
+      const int32_t* p = (const int32_t*)r->b_rp;
+      r->rp.resize(r->n + 1);
+      for (int64_t i = 0; i <= r->n; ++i) r->rp[i] = p[i];
+    }
+  }
+  const int64_t* h_rp = (r->borrowed && r->b_index64) ? (const int64_t*)r->b_rp : r->rp.data();
+  const int32_t* h_col = r->borrowed ? r->b_col : r->col.data();
+  const float* h_val = r->borrowed ? r->b_val : r->val.data();
+  const float* h_U0 = r->borrowed ? r->b_U0 : r->U0.data();
   float* d_U0 = nullptr;
   cudaError_t e = cudaMalloc(&r->d_rp, sizeof(int64_t) * (r->n + 1));
   if (e == cudaSuccess && r->nnz > 0) e = cudaMalloc(&r->d_col, sizeof(int32_t) * r->nnz);
   if (e == cudaSuccess && r->nnz > 0) e = cudaMalloc(&r->d_val, sizeof(float) * r->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&d_U0, sizeof(float) * r->n * r->k);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_rp, r->rp.data(), sizeof(int64_t) * (r->n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_rp, h_rp, sizeof(int64_t) * (r->n + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && r->nnz > 0)
-    e = cudaMemcpyAsync(r->d_col, r->col.data(), sizeof(int32_t) * r->nnz, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(r->d_col, h_col, sizeof(int32_t) * r->nnz, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && r->nnz > 0)
-    e = cudaMemcpyAsync(r->d_val, r->val.data(), sizeof(float) * r->nnz, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_U0, r->U0.data(), sizeof(float) * r->n * r->k, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(r->d_val, h_val, sizeof(float) * r->nnz, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_U0, h_U0, sizeof(float) * r->n * r->k, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     if (d_U0) cudaFree(d_U0);
     set_error("admission: %s", cudaGetErrorString(e));
@@ -158,6 +181,15 @@ static cluster_status admit(cluster_server* sv, Request* r, cudaStream_t s) {
   cluster_status st = r->ctx ? init_impl(&S, r->k, d_U0, &o, s, r->ctx, false) : CLUSTER_ENOMEM;
   cudaStreamSynchronize(s);
   cudaFree(d_U0);
+  // the device has its own copy now
+  r->rp.clear();
+  r->rp.shrink_to_fit();
+  r->col.clear();
+  r->col.shrink_to_fit();
+  r->val.clear();
+  r->val.shrink_to_fit();
+  r->U0.clear();
+  r->U0.shrink_to_fit();
   return st;
 }
 
@@ -197,6 +229,7 @@ static void worker_main(cluster_server* sv) {
         while (!sv->queue.empty()) {
           Request* r = sv->queue.front();
           sv->queue.pop_front();
+          sv->queued_host -= r->host_bytes;
           finish(sv, r, CLUSTER_ECUDA, "server could not create its CUDA stream");
         }
         sv->cv_done.notify_all();
@@ -209,6 +242,7 @@ static void worker_main(cluster_server* sv) {
         Request* r = sv->queue.front();
         if (r->footprint > sv->opt.hbm_budget) {  // can never fit
           sv->queue.pop_front();
+          sv->queued_host -= r->host_bytes;
           finish(sv, r, CLUSTER_ENOMEM, "request needs more device memory than the server budget");
           continue;
         }
@@ -217,6 +251,7 @@ static void worker_main(cluster_server* sv) {
         if (sv->used + r->footprint > sv->opt.hbm_budget) break;
         sv->queue.pop_front();
         sv->used += r->footprint;
+        sv->queued_host -= r->host_bytes;
         admits.push_back(r);
       }
       sv->cv_done.notify_all();
@@ -300,6 +335,7 @@ static void worker_main(cluster_server* sv) {
     while (!sv->queue.empty()) {
       Request* r = sv->queue.front();
       sv->queue.pop_front();
+      sv->queued_host -= r->host_bytes;
       finish(sv, r, CLUSTER_EAGAIN, "server shut down before the request was admitted");
     }
     sv->cv_done.notify_all();
@@ -371,24 +407,45 @@ extern "C" cluster_status cluster_server_submit(cluster_server* sv, const cluste
     set_error("out of host memory");
     return CLUSTER_ENOMEM;
   }
-  try {
-    r->n = S->n;
-    r->nnz = S->nnz;
-    r->k = k;
-    r->rp.resize(S->n + 1);
-    if (S->index64) {
-      memcpy(r->rp.data(), S->row_ptr, sizeof(int64_t) * (S->n + 1));
-    } else {
-      const int32_t* p = (const int32_t*)S->row_ptr;
-      for (int64_t i = 0; i <= S->n; ++i) r->rp[i] = p[i];
+  r->n = S->n;
+  r->nnz = S->nnz;
+  r->k = k;
+  const size_t bytes = 8 * (size_t)(S->n + 1) + 8 * (size_t)S->nnz + 4 * (size_t)S->n * k;
+  if (sv->opt.borrow_host) {
+    r->borrowed = true;
+    r->b_rp = S->row_ptr;
+    r->b_index64 = S->index64;
+    r->b_col = S->col;
+    r->b_val = S->val;
+    r->b_U0 = U0;
+  } else {
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      // an empty queue always takes one request, however large
+      if (sv->opt.queue_bytes_max > 0 && sv->queued_host > 0 && sv->queued_host + bytes > sv->opt.queue_bytes_max) {
+        sv->stats.rejected++;
+        delete r;
+        set_error("queue full: %zu bytes of requests wait for admission", sv->queued_host);
+        return CLUSTER_EAGAIN;
+      }
     }
-    r->col.assign(S->col, S->col + S->nnz);
-    r->val.assign(S->val, S->val + S->nnz);
-    r->U0.assign(U0, U0 + S->n * k);
-  } catch (...) {
-    delete r;
-    set_error("out of host memory");
-    return CLUSTER_ENOMEM;
+    try {
+      r->rp.resize(S->n + 1);
+      if (S->index64) {
+        memcpy(r->rp.data(), S->row_ptr, sizeof(int64_t) * (S->n + 1));
+      } else {
+        const int32_t* p = (const int32_t*)S->row_ptr;
+        for (int64_t i = 0; i <= S->n; ++i) r->rp[i] = p[i];
+      }
+      r->col.assign(S->col, S->col + S->nnz);
+      r->val.assign(S->val, S->val + S->nnz);
+      r->U0.assign(U0, U0 + S->n * k);
+    } catch (...) {
+      delete r;
+      set_error("out of host memory");
+      return CLUSTER_ENOMEM;
+    }
+    r->host_bytes = bytes;
   }
   r->footprint = footprint(r->n, r->nnz, k, sv->opt.solve);
   r->t_submit = now_s();
@@ -399,6 +456,7 @@ extern "C" cluster_status cluster_server_submit(cluster_server* sv, const cluste
       set_error("server is shutting down");
       return CLUSTER_EAGAIN;
     }
+    sv->queued_host += r->host_bytes;
     r->ticket = sv->next_ticket++;
     sv->all[r->ticket] = r;
     sv->queue.push_back(r);
@@ -464,6 +522,7 @@ extern "C" cluster_status cluster_server_get_stats(cluster_server* sv, cluster_s
   *out = sv->stats;
   out->queued = (int64_t)sv->queue.size();
   out->budget_bytes = sv->opt.hbm_budget;
+  out->queued_host_bytes = sv->queued_host;
   out->uptime_s = now_s() - sv->busy_t0;
   return CLUSTER_OK;
 }

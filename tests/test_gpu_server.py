@@ -117,3 +117,28 @@ def test_wait_times_out_then_succeeds():
     U, rep, _ = srv.wait(t, timeout=300)
     assert rep["iters"] == 400
     srv.close()
+
+
+def test_queue_cap_refuses_and_borrowed_inputs_work():
+    reqs = [_host(s) for s in SPECS[:3]]
+    # copied requests: a queue cap below one request's host bytes refuses submissions beyond the first
+    srv = pkg.Server(iters_per_tick=4, max_resident=1, queue_bytes_max=1, stop_rule=3, max_iter=200)
+    accepted, refused = [], 0
+    for r in [reqs[2], reqs[0], reqs[1]]:
+        try:
+            accepted.append(srv.submit(*r))
+        except pkg.ClusterError as exc:
+            assert exc.status == pkg.EAGAIN and "queue full" in str(exc)
+            refused += 1
+    for t in accepted:
+        srv.wait(t, timeout=120)
+    assert srv.stats()["rejected"] == refused >= 1
+    srv.close()
+    # borrowed host inputs give the same results as copied ones
+    srv = pkg.Server(iters_per_tick=8, borrow_host=True, **OPTS)
+    ts = [srv.submit(*r) for r in reqs]
+    outs = [srv.wait(t, timeout=300) for t in ts]
+    srv.close()
+    for r, (U, rep, _) in zip(reqs, outs):
+        Us, _ = _solo(*r, **OPTS)
+        assert np.array_equal(U, Us)
