@@ -214,6 +214,78 @@ __device__ __forceinline__ float team_sum(float v) {
   return v;
 }
 
+// ---- warp-level tensor-core helpers (mma.sync m16n8k8, TF32 inputs, FP32 accumulate) ----
+// Fragment layout (lane = 4 g + t): A 16x8 row-major a0 = A[g][t], a1 = A[g+8][t],
+// a2 = A[g][t+4], a3 = A[g+8][t+4]; B 8x8 b0 = B[t][g], b1 = B[t+4][g];
+// D 16x8 d0 = D[g][2t], d1 = D[g][2t+1], d2 = D[g+8][2t], d3 = D[g+8][2t+1].
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x ~ hi + lo with both parts TF32 values (the 3xTF32 split; hi keeps the top
+// 11 significant bits, lo the next 11, so hi + lo carries about 22 bits of x)
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x) & 0xffffe000u;
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Tensor-core layout of the update for 16 <= KP <= 64.  Y G: the R x KP tile
+// of extrapolated rows times G(Y) as (R/16) x (KP/8) output blocks, one per
+// warp.  Gram matrices: 16 x 8 feature blocks, TB of them, spread over the
+// warps (BPW per warp, consecutive blocks sharing their A fragment); when
+// there are fewer blocks than warps the tile rows are split KSPLIT ways and the
+// partial blocks summed at the end in a fixed order.  Every product is 3xTF32
+// (x = hi + lo, hi*hi + hi*lo + lo*hi), with the split done once when a value
+// is written to shared memory.  Strides: TSA (= 4 mod 32 in words) makes the
+// row-major fragment reads conflict-free, TSB (= 8 mod 16) the transposed
+// Gram reads and the float2 stores of Y G.
+template <int KP, bool EVAL>
+struct MmaLay {
+  static constexpr bool ON = KP >= 16 && KP <= 64;
+  static constexpr int TSA = KP + 4;
+  static constexpr int TSB = KP + 8;
+  static constexpr int KS = KP / 8;                     // K steps of Y G
+  static constexpr int MATS = EVAL ? 1 : 2;
+  static constexpr int GBLK = ON ? (KP / 16) * (KP / 8) : 1;  // 16x8 blocks per matrix
+  static constexpr int TB = MATS * GBLK;
+  static constexpr int WARPS = Lay<KP>::WARPS;
+  static constexpr int KSPLIT = TB >= WARPS ? 1 : WARPS / TB;
+  static constexpr int BPW = TB >= WARPS ? TB / WARPS : 1;
+  static constexpr int RS = Lay<KP>::R / 8;             // K steps of a Gram over one tile
+  static_assert(!ON || (Lay<KP>::R % 16 == 0 && (Lay<KP>::R / 16) * KS == WARPS), "Y G blocks != warps");
+  static_assert(!ON || (TB % WARPS == 0 || WARPS % TB == 0), "Gram blocks do not tile the warps");
+  static_assert(!ON || RS % KSPLIT == 0, "row split");
+  static_assert(!ON || BPW == 1 || (KP / 8) % BPW == 0, "blocks of a warp share one A fragment");
+  // shared floats: G fragments (2 KP^2 unless eval), Y hi/lo (TSA), Y G and
+  // four hi/lo tiles of Xbar^n and Y^{n+1} (TSB)
+  __host__ __device__ static constexpr size_t floats(bool eval) {
+    return (eval ? 0 : 2 * (size_t)KP * KP) + 2 * (size_t)Lay<KP>::R * TSA + 5 * (size_t)Lay<KP>::R * TSB;
+  }
+};
+
+__device__ __forceinline__ void split_store4(float* hi, float* lo, const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split_tf32(v[q], h[q], l[q]);
+  *reinterpret_cast<uint4*>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void mma3_tf32(float* d, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                                          const uint32_t* bl) {
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
 // acc += sum_{e in [lo, hi)} val[e] * Xg[col[e], f0 .. f0+VEC).  `batches` must
 // be the same on every lane of the warp (the maximum over its teams).  The
 // (col, val) pairs of batch j+1 are fetched while the gathers of batch j are in
@@ -310,8 +382,9 @@ __device__ __forceinline__ void project_simplex(const float* v, float* x, int f0
 template <int KP>
 __host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
   using L = Lay<KP>;
-  // Gy (KP*KP) unless eval, then three R x KP tiles (xn, yn, ys), which the
-  // end-of-kernel Gram group reduction reuses
+  // Gy (KP*KP) unless eval, then the R-row tiles (xn, yn, ys [, q]), which the
+  // end-of-kernel reductions reuse
+  if (MmaLay<KP, false>::ON) return sizeof(float) * MmaLay<KP, false>::floats(eval) + 64;
   const size_t tiles = 3 * (size_t)L::R * KP;
   const size_t red = eval ? (size_t)GramLay<KP, true>::ACTIVE * GramLay<KP, true>::BS * GramLay<KP, true>::BS
                           : (size_t)GramLay<KP, false>::ACTIVE * GramLay<KP, false>::BS * GramLay<KP, false>::BS;
@@ -340,22 +413,58 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
   __nv_bfloat16* XSo = (pass & 1) ? a.XS0 : a.XS1;
 
-  float* Gs = smem;
-  float* xn_t = Gs + (EVAL ? 0 : L::E2);
-  float* yn_t = xn_t + L::R * KP;
-  float* ys = yn_t + L::R * KP;
-
+  using M = MmaLay<KP, EVAL>;
+  constexpr int TS = M::ON ? M::TSB : KP;  // stride of the xn / yn tiles
   const int tid = threadIdx.x;
-  if constexpr (!EVAL) {
-    for (int e = tid; e < L::E2; e += L::NT) Gs[e] = a.Gy[e];
-  }
-  __syncthreads();
-
   const int warp = tid >> 5, lane = tid & 31;
   const int tiw = lane / L::T, lt = lane % L::T;
   const int team = warp * L::TPW + tiw;
   const int f0 = lt * L::VEC;
   const int k = a.k;
+  const int mg = lane >> 2, mt = lane & 3;  // mma fragment coordinates (lane = 4 mg + mt)
+
+  // shared memory.  FFMA path: Gs | xn | yn | ys.  MMA path: G fragments |
+  // Y hi | Y lo | Y G | Xbar^n hi | lo | Y^{n+1} hi | lo.
+  float* Gs = smem;
+  uint4* Gf = reinterpret_cast<uint4*>(smem);
+  float* tiles = smem + (EVAL ? 0 : (M::ON ? 2 * L::E2 : L::E2));
+  float* ys = tiles + (M::ON ? 0 : 2 * L::R * KP);
+  float* ysl = ys + L::R * M::TSA;
+  float* qs = ysl + L::R * M::TSA;
+  float* xn_t = M::ON ? qs + L::R * TS : tiles;
+  float* xn_l = xn_t + L::R * TS;
+  float* yn_t = M::ON ? xn_l + L::R * TS : tiles + L::R * KP;
+  float* yn_l = yn_t + L::R * TS;
+
+  // Y G block of this warp (MMA path): rows 16 ym .. +16, columns 8 yn .. +8
+  const int ym = M::ON ? warp / M::KS : 0, yn = M::ON ? warp % M::KS : 0;
+  if constexpr (!EVAL) {
+    if constexpr (M::ON) {
+      // B fragments of G(Y), split hi/lo once: Gf[(yb * KS + ks) * 32 + lane]
+      for (int e = tid; e < M::KS * M::KS * 32; e += L::NT) {
+        const int ln = e & 31, ks = (e >> 5) % M::KS, yb = (e >> 5) / M::KS;
+        const int r0 = 8 * ks + (ln & 3), c0 = 8 * yb + (ln >> 2);
+        uint32_t h0, l0, h1, l1;
+        split_tf32(a.Gy[r0 * KP + c0], h0, l0);
+        split_tf32(a.Gy[(r0 + 4) * KP + c0], h1, l1);
+        Gf[e] = make_uint4(h0, h1, l0, l1);
+      }
+    } else {
+      for (int e = tid; e < L::E2; e += L::NT) Gs[e] = a.Gy[e];
+    }
+  }
+  __syncthreads();
+
+  // Gram blocks of this warp (MMA path)
+  const int mb0 = M::ON ? (warp % (M::TB / M::BPW)) * M::BPW : 0;   // first block
+  const int mks = M::ON ? warp / (M::TB / M::BPW) : 0;                // row-split part
+  const bool mon = M::ON && mb0 < M::TB;
+  const int mmat = mb0 / (M::GBLK > 0 ? M::GBLK : 1);
+  const int mrem = mb0 % (M::GBLK > 0 ? M::GBLK : 1);
+  const int mmi = mrem / (KP / 8 > 0 ? KP / 8 : 1), mnj0 = mrem % (KP / 8 > 0 ? KP / 8 : 1);
+  float macc[M::ON ? M::BPW : 1][4];
+#pragma unroll
+  for (int j = 0; j < (M::ON ? M::BPW : 1); ++j) macc[j][0] = macc[j][1] = macc[j][2] = macc[j][3] = 0.f;
 
   // Gram tasks of this thread (see GramLay)
   using G = GramLay<KP, EVAL>;
@@ -437,24 +546,46 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
         y[q] = fmaf(beta, pv[q] - qv[q], pv[q]);
         sy[q] = fmaf(beta, acc[q] - zp[q], acc[q]);
       }
-      float* yrow = ys + team * KP;
-#pragma unroll
-      for (int q = 0; q < L::VEC; ++q) yrow[f0 + q] = y[q];
-      __syncwarp();
       // q_b = sum_a y_a G[a][b] for this lane's b in [f0, f0 + VEC)
       float qq[L::VEC];
+      if constexpr (M::ON) {
+        // tile product Y G on tensor cores (3xTF32)
+        split_store4(ys + team * M::TSA + f0, ysl + team * M::TSA + f0, y);
+        __syncthreads();
+        float dq[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint32_t* yh = reinterpret_cast<const uint32_t*>(ys) + (16 * ym + mg) * M::TSA + mt;
+        const uint32_t* yl = reinterpret_cast<const uint32_t*>(ysl) + (16 * ym + mg) * M::TSA + mt;
 #pragma unroll
-      for (int q = 0; q < L::VEC; ++q) qq[q] = 0.f;
+        for (int ks = 0; ks < M::KS; ++ks) {
+          const uint32_t ah[4] = {yh[8 * ks], yh[8 * M::TSA + 8 * ks], yh[8 * ks + 4], yh[8 * M::TSA + 8 * ks + 4]};
+          const uint32_t al[4] = {yl[8 * ks], yl[8 * M::TSA + 8 * ks], yl[8 * ks + 4], yl[8 * M::TSA + 8 * ks + 4]};
+          const uint4 g = Gf[(yn * M::KS + ks) * 32 + lane];
+          const uint32_t bh[2] = {g.x, g.y}, bl[2] = {g.z, g.w};
+          mma3_tf32(dq, ah, al, bh, bl);
+        }
+        float* qo = qs + (16 * ym + mg) * TS + 8 * yn + 2 * mt;
+        *reinterpret_cast<float2*>(qo) = make_float2(dq[0], dq[1]);
+        *reinterpret_cast<float2*>(qo + 8 * TS) = make_float2(dq[2], dq[3]);
+        __syncthreads();
+        load_row<L::VEC>(qs + team * TS + f0, qq);
+      } else {
+        float* yrow = ys + team * KP;
+#pragma unroll
+        for (int q = 0; q < L::VEC; ++q) yrow[f0 + q] = y[q];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < L::VEC; ++q) qq[q] = 0.f;
 #pragma unroll 4
-      for (int a4 = 0; a4 < KP; a4 += L::VEC) {
-        float ya[L::VEC];
-        load_row<L::VEC>(yrow + a4, ya);
+        for (int a4 = 0; a4 < KP; a4 += L::VEC) {
+          float ya[L::VEC];
+          load_row<L::VEC>(yrow + a4, ya);
 #pragma unroll
-        for (int aa = 0; aa < L::VEC; ++aa) {
-          float g[L::VEC];
-          load_row<L::VEC>(Gs + (a4 + aa) * KP + f0, g);
+          for (int aa = 0; aa < L::VEC; ++aa) {
+            float g[L::VEC];
+            load_row<L::VEC>(Gs + (a4 + aa) * KP + f0, g);
 #pragma unroll
-          for (int q = 0; q < L::VEC; ++q) qq[q] = fmaf(ya[aa], g[q], qq[q]);
+            for (int q = 0; q < L::VEC; ++q) qq[q] = fmaf(ya[aa], g[q], qq[q]);
+          }
         }
       }
       float v[L::VEC], x[L::VEC];
@@ -477,26 +608,67 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
       }
       // next pass's extrapolated row y^{n+1} = xbar^n + beta_{n+1} (xbar^n - xbar^{n-1}),
       // formed exactly as the next pass will form it, feeds G(Y^{n+1})
+      float xv[L::VEC], yv[L::VEC];
 #pragma unroll
       for (int q = 0; q < L::VEC; ++q) {
-        xn_t[team * KP + f0 + q] = active ? x[q] : 0.f;
-        yn_t[team * KP + f0 + q] = active ? fmaf(beta_next, x[q] - pv[q], x[q]) : 0.f;
+        xv[q] = active ? x[q] : 0.f;
+        yv[q] = active ? fmaf(beta_next, x[q] - pv[q], x[q]) : 0.f;
+      }
+      if constexpr (M::ON) {
+        split_store4(xn_t + team * TS + f0, xn_l + team * TS + f0, xv);
+        split_store4(yn_t + team * TS + f0, yn_l + team * TS + f0, yv);
+      } else {
+        store_row<L::VEC>(xn_t + team * TS + f0, xv);
+        store_row<L::VEC>(yn_t + team * TS + f0, yv);
       }
     } else {
+      float xv[L::VEC];
 #pragma unroll
       for (int q = 0; q < L::VEC; ++q) {
-        xn_t[team * KP + f0 + q] = active ? pv[q] : 0.f;
+        xv[q] = active ? pv[q] : 0.f;
         if (active && !isfinite(acc[q])) bad = 1;
       }
+      if constexpr (M::ON) split_store4(xn_t + team * TS + f0, xn_l + team * TS + f0, xv);
+      else store_row<L::VEC>(xn_t + team * TS + f0, xv);
     }
     __syncthreads();
-    // symmetric Gram blocks: M[I-block][J-block] += m_r[I-block] (x) m_r[J-block]
-    if (gact) {
+    if constexpr (M::ON) {
+      // Gram blocks on tensor cores: D[m][n] += sum_r T[r][m] T[r][n] over this
+      // warp's share of the tile rows (A = T^T rows 16 mmi.., B = T columns 8 nj..)
+      // The tensor core's accumulator addition does not round to nearest, so a
+      // long running sum in it drifts; each tile's blocks start from zero and
+      // are added to the running sums with ordinary float adds.
+      if (mon) {
+        const uint32_t* th = reinterpret_cast<const uint32_t*>(mmat ? yn_t : xn_t);
+        const uint32_t* tl = reinterpret_cast<const uint32_t*>(mmat ? yn_l : xn_l);
+        float dt[M::BPW][4];
+#pragma unroll
+        for (int j = 0; j < M::BPW; ++j) dt[j][0] = dt[j][1] = dt[j][2] = dt[j][3] = 0.f;
+#pragma unroll
+        for (int rs = mks * (M::RS / M::KSPLIT); rs < (mks + 1) * (M::RS / M::KSPLIT); ++rs) {
+          const int o0 = (8 * rs + mt) * TS, o4 = o0 + 4 * TS;
+          const int ca = 16 * mmi + mg;
+          const uint32_t ah[4] = {th[o0 + ca], th[o0 + ca + 8], th[o4 + ca], th[o4 + ca + 8]};
+          const uint32_t al[4] = {tl[o0 + ca], tl[o0 + ca + 8], tl[o4 + ca], tl[o4 + ca + 8]};
+#pragma unroll
+          for (int j = 0; j < M::BPW; ++j) {
+            const int cb = 8 * (mnj0 + j) + mg;
+            const uint32_t bh[2] = {th[o0 + cb], th[o4 + cb]}, bl[2] = {tl[o0 + cb], tl[o4 + cb]};
+            mma3_tf32(dt[j], ah, al, bh, bl);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < M::BPW; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) macc[j][q] += dt[j][q];
+      }
+    } else if (gact) {
+      // symmetric Gram blocks: M[I-block][J-block] += m_r[I-block] (x) m_r[J-block]
       for (int r = ggrp; r < L::R; r += G::GROUPS) {
 #pragma unroll
         for (int j = 0; j < G::TPT; ++j) {
           if (!gOn[j]) continue;
-          const float* src = (gM[j] ? yn_t : xn_t) + r * KP;
+          const float* src = (gM[j] ? yn_t : xn_t) + r * TS;
           float xa[BS], xb[BS];
           load_row<BS>(src + gI[j] * BS, xa);
           load_row<BS>(src + gJ[j] * BS, xb);
@@ -507,8 +679,11 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
         }
       }
     }
-    __syncthreads();
+    // MMA update path: the next tile's first two barriers already order its
+    // tile writes after these Gram reads
+    if constexpr (!M::ON || EVAL) __syncthreads();
   }
+  if constexpr (M::ON && !EVAL) __syncthreads();
 
   // ---- block reductions (fixed order => bit-reproducible) ----
   double* dred = reinterpret_cast<double*>(xn_t);  // reuse tile memory
@@ -538,7 +713,36 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   }
   __syncthreads();
   float* gout = a.gram_part + (size_t)slot * 2 * L::E2;
-  if constexpr (G::GROUPS == 1) {
+  if constexpr (M::ON) {
+    // block (mat, 16 mi.., 8 nj..) of fragment lane (mg, mt): rows mg, mg + 8, columns 2 mt, 2 mt + 1
+    if constexpr (M::KSPLIT == 1) {
+#pragma unroll
+      for (int j = 0; j < M::BPW; ++j) {
+        float* o = gout + mmat * L::E2 + (16 * mmi + mg) * KP + 8 * (mnj0 + j) + 2 * mt;
+        *reinterpret_cast<float2*>(o) = make_float2(macc[j][0], macc[j][1]);
+        *reinterpret_cast<float2*>(o + 8 * KP) = make_float2(macc[j][2], macc[j][3]);
+      }
+    } else {
+      // row-split partials: stage [part][block][lane][4], then sum parts in order
+      float* red = tiles;
+      if (mon) *reinterpret_cast<float4*>(red + ((mks * M::TB + mb0) * 32 + lane) * 4) =
+          make_float4(macc[0][0], macc[0][1], macc[0][2], macc[0][3]);
+      __syncthreads();
+      for (int e = tid; e < M::TB * 32; e += L::NT) {
+        float4 sum = *reinterpret_cast<const float4*>(red + e * 4);
+#pragma unroll
+        for (int pp = 1; pp < M::KSPLIT; ++pp) {
+          const float4 v = *reinterpret_cast<const float4*>(red + ((pp * M::TB) * 32 + e) * 4);
+          sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+        }
+        const int blk = e >> 5, ln = e & 31;
+        const int mat = blk / M::GBLK, rem = blk % M::GBLK;
+        float* o = gout + mat * L::E2 + (16 * (rem / (KP / 8)) + (ln >> 2)) * KP + 8 * (rem % (KP / 8)) + 2 * (ln & 3);
+        *reinterpret_cast<float2*>(o) = make_float2(sum.x, sum.y);
+        *reinterpret_cast<float2*>(o + 8 * KP) = make_float2(sum.z, sum.w);
+      }
+    }
+  } else if constexpr (G::GROUPS == 1) {
 #pragma unroll
     for (int j = 0; j < G::TPT; ++j) {
       if (!gOn[j]) continue;
@@ -776,7 +980,6 @@ __host__ __device__ constexpr int fold_blocks(bool eval) {
 template <int KP>
 __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblocks) {
   constexpr int E2 = KP * KP;
-  constexpr int BS = KP < 4 ? KP : 4;
   FistaState* st = f.st;
   volatile FistaState* vs = st;
   if (!f.eval && (vs->done || vs->pass >= vs->limit)) return;
@@ -787,7 +990,7 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   const int e = blk * 256 + tid;
   if (e < nent) {
     const int m = e / E2, r = (e % E2) / KP, c = e % KP;
-    const int src = m * E2 + ((r / BS <= c / BS) ? r * KP + c : c * KP + r);
+    const int src = m * E2 + ((r <= c) ? r * KP + c : c * KP + r);
     double s = 0.0;
     for (int p = 0; p < f.parts; ++p) s += (double)f.gram_part[(size_t)p * 2 * E2 + src];
     (m == 0 ? f.A : f.G)[r * KP + c] = s;

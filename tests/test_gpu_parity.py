@@ -295,9 +295,27 @@ def test_sampled_rows_at_one_million_articles():
     X2 = s.get_U().cpu().numpy()
     s.step(1)
     X1 = s.get_U().cpu().numpy()
-    s.step(1)
+    rep = s.step(1)
     X0 = s.get_U().cpu().numpy()
     S = to_scipy(rp, c, v, n)
+    # loss terms in float64: each update block sums thousands of rows here, so
+    # a drifting accumulation shows up well above ordinary float32 rounding
+    S2 = float((S.data.astype(np.float64) ** 2).sum())
+
+    def loss_terms(X):
+        Xd = X.astype(np.float64)
+        Gm = Xd.T @ Xd
+        gram2 = float((Gm * Gm).sum())
+        tr = float((Xd * (S @ Xd)).sum())
+        return gram2, tr, S2 - 2.0 * tr + gram2
+
+    assert rep["f_iter"] == m - 1         # the pass that formed Xbar^m evaluated f(Xbar^{m-1})
+    gram2, tr, f = loss_terms(X1)
+    assert abs(rep["gram_fro2"] - gram2) <= 2e-5 * gram2
+    assert abs(rep["trace_SU"] - tr) <= 2e-5 * tr
+    assert abs(rep["f"] - f) <= 2e-5 * f
+    f0 = loss_terms(X0)[2]
+    assert abs(pkg.objective(rp, c, v, s.get_U()) - f0) <= 2e-5 * f0
     tau = 1.0 / oracle.lipschitz(S)
     beta = oracle.momentum_factors(m)[m - 1]
     deg = np.diff(S.indptr)
