@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "PG iters/s, mixed vs FP32, at equal objective (n=70M,k=32); serving p99 latency"
 UNIT = "iter/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k32_n70M.json")
-PASS_SRC = os.path.join(ROOT, "paper_2506_04045_b300", "csrc", "pass_kernels.cuh")
+SPMM_SRC = [os.path.join(ROOT, "paper_2506_04045_b300", "csrc", f) for f in ("iter_common.cuh", "spmm_kernels.cuh", "state.h")]
 
 
 def parse():
@@ -163,8 +163,13 @@ def update_bytes(n, k, mixed):
 
 
 def kernel_digest() -> str:
-    with open(PASS_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Digest of the dominant (gather) kernel's sources: the traffic figures
+    stay valid while these files are unchanged."""
+    h = hashlib.sha256()
+    for path in SPMM_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def traffic_for(form: str, workload: str):

@@ -82,7 +82,10 @@ struct BOps {
     else batch_update_kernel<KP, false><<<bc.upd_grid, L::NT, smem, s>>>(bc.meta);
     batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
   }
-  static int64_t units(const cluster_ctx* c) { return spmm_units<KP>(c->n, c->n_heavy, c->n_chunks); }
+  static int64_t units(const cluster_ctx* c) {
+    return c->mixed ? spmm_units<KP, true>(c->n, c->n_heavy, c->n_chunks)
+                    : spmm_units<KP, false>(c->n, c->n_heavy, c->n_chunks);
+  }
   // one iteration with events around the two persistent kernels
   static void timed_iteration(const BatchClass& bc, int spmm_grid, int upd_grid, cudaEvent_t* ev, cudaStream_t s) {
     cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);

@@ -23,42 +23,17 @@
 // f(Xbar^{n-1}) = ||S||^2 - 2 sum_i p_i + ||Xbar^{n-1 T} Xbar^{n-1}||^2 is the
 // trace identity of Sect. 3 ("Loss Update").
 //
-// Layout: a "team" of T lanes owns one row; lane t holds VEC consecutive
-// features.  Teams of one warp take rows of similar degree (rows are visited in
-// degree order), so the gather loop is warp-uniform.  Rows are grouped into
-// tiles of R rows per block; after each tile the block adds the tile's outer
-// products into per-thread float32 Gram accumulators (upper blocks only).  Rows of very high
-// degree are split into chunks whose partial products are computed by
-// heavy_kernel just before the pass.
+// Rows are grouped into tiles of R rows per block (team layout: iter_common.cuh).
+// For 16 <= KP <= 64 the tile's dense contractions (Y G and the two Gram
+// accumulations) run on the tensor cores (warp-level mma, 3xTF32); otherwise
+// each thread accumulates float32 blocks of the upper Gram triangle.  Rows of
+// very high degree are split into chunks whose partial products are computed
+// before the row's update (heavy_kernel, or spmm_kernel in the split form).
 #pragma once
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "state.h"
+#include "iter_common.cuh"
+#include "spmm_kernels.cuh"
 
 namespace fc {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-#ifndef FC_MINB32
-#define FC_MINB32 4  // resident 256-thread blocks per SM the k <= 32 pass is sized for
-#endif
-
-template <int KP>
-struct Lay {
-  static constexpr int VEC = KP < 4 ? KP : 4;      // features per lane
-  static constexpr int T = KP / VEC;                // lanes per team (row)
-  static constexpr int TPW = 32 / T;                // teams per warp
-  static constexpr int NT = KP >= 128 ? 512 : 256;  // threads per block
-  static constexpr int WARPS = NT / 32;
-  static constexpr int R = WARPS * TPW;             // rows per tile
-  static constexpr int NB = T > 8 ? T : 8;          // nonzeros per gather batch per team
-  static constexpr int PER = NB / T;                // (col, val) pairs each lane fetches per batch
-  static constexpr int E2 = KP * KP;
-  // resident blocks per SM the register budget is sized for
-  static constexpr int MINB = KP <= 4 ? 2 : (KP == 8 ? 3 : (KP == 16 ? 4 : (KP == 32 ? FC_MINB32 : (KP == 64 ? 2 : 1))));
-};
 
 // Symmetric Gram accumulation: the KP x KP matrix is cut into BS x BS blocks
 // and only blocks (I, J) with I <= J are accumulated ("tasks"); the fold
@@ -89,129 +64,6 @@ __device__ __forceinline__ void gram_task(int t, int nblk, int nb1, int& m, int&
     ++I;
   }
   J = I + bi;
-}
-
-struct PassArgs {
-  const int64_t* row_ptr;    // [n+1]
-  const int32_t* col;        // [nnz]
-  const void* val;           // [nnz] float32 (FP32) or bfloat16 (mixed)
-  const int32_t* order;      // rows in processing order (nullptr: identity)
-  const int64_t* cta_pos;    // [gridDim.x + 1] position ranges (nullptr: even split)
-  int64_t n_heavy;           // positions [0, n_heavy) are chunked rows
-  const int64_t* chunk_ptr;  // [n_heavy + 1]
-  const int64_t* chunk_e0;   // [n_chunks]
-  const int64_t* chunk_e1;   // [n_chunks]
-  int64_t n_chunks;
-  float* hv_part;            // [n_chunks][KP] partial products of chunked rows
-  float* X0;                 // iterate buffers, n x KP float32 (Xbar^j in X_{j&1})
-  float* X1;
-  __nv_bfloat16* XS0;        // bfloat16 gather copies (mixed precision)
-  __nv_bfloat16* XS1;
-  float* Zp;                 // fused pass: n x KP S Xbar^{pass-1}, replaced by S Xbar^{pass}
-  float* Z0;                 // split pass: S Xbar^j in Z_{(j+1)&1}, n x KP float32
-  float* Z1;
-  unsigned long long* work;  // split pass: work counter of spmm_kernel (reset by the fold)
-  const float* Gy;           // KP x KP float32, G(Y) minus its mean entry
-  float* gram_part;          // [gridDim.x][2][KP][KP]
-  double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite
-  FistaState* st;
-  int64_t n;
-  int32_t k;
-  int32_t eval_sel;          // objective-only pass: buffer index to evaluate
-};
-
-template <bool MIXED>
-struct GatherT;
-template <>
-struct GatherT<false> {
-  using V = float;
-};
-template <>
-struct GatherT<true> {
-  using V = __nv_bfloat16;
-};
-
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// Load VEC consecutive features of the gathered iterate at element offset off.
-template <int VEC, bool MIXED>
-__device__ __forceinline__ void load_feat(const void* Xg, int64_t off, float* out) {
-  if constexpr (!MIXED) {
-    const float* p = reinterpret_cast<const float*>(Xg) + off;
-    if constexpr (VEC == 4) {
-      float4 v = __ldg(reinterpret_cast<const float4*>(p));
-      out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-    } else if constexpr (VEC == 2) {
-      float2 v = __ldg(reinterpret_cast<const float2*>(p));
-      out[0] = v.x; out[1] = v.y;
-    } else {
-      out[0] = __ldg(p);
-    }
-  } else {
-    const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(Xg) + off;
-    if constexpr (VEC == 4) {
-      uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
-      __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&raw.x);
-      __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&raw.y);
-      float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-      out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
-    } else if constexpr (VEC == 2) {
-      unsigned raw = __ldg(reinterpret_cast<const unsigned*>(p));
-      float2 f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw));
-      out[0] = f.x; out[1] = f.y;
-    } else {
-      out[0] = __bfloat162float(p[0]);
-    }
-  }
-}
-
-template <int VEC>
-__device__ __forceinline__ void load_row(const float* base, float* out) {
-  if constexpr (VEC == 4) {
-    float4 v = *reinterpret_cast<const float4*>(base);
-    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-  } else if constexpr (VEC == 2) {
-    float2 v = *reinterpret_cast<const float2*>(base);
-    out[0] = v.x; out[1] = v.y;
-  } else {
-    out[0] = base[0];
-  }
-}
-
-template <int VEC>
-__device__ __forceinline__ void store_row(float* base, const float* v) {
-  if constexpr (VEC == 4) {
-    *reinterpret_cast<float4*>(base) = make_float4(v[0], v[1], v[2], v[3]);
-  } else if constexpr (VEC == 2) {
-    *reinterpret_cast<float2*>(base) = make_float2(v[0], v[1]);
-  } else {
-    base[0] = v[0];
-  }
-}
-
-template <int VEC>
-__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* base, const float* v) {
-  if constexpr (VEC == 4) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
-    __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
-    uint2 raw;
-    raw.x = *reinterpret_cast<unsigned*>(&a);
-    raw.y = *reinterpret_cast<unsigned*>(&b);
-    *reinterpret_cast<uint2*>(base) = raw;
-  } else if constexpr (VEC == 2) {
-    *reinterpret_cast<__nv_bfloat162*>(base) = __floats2bfloat162_rn(v[0], v[1]);
-  } else {
-    base[0] = __float2bfloat16_rn(v[0]);
-  }
-}
-
-// Sum over the T lanes of a team (teams are aligned groups of T lanes).
-template <int T>
-__device__ __forceinline__ float team_sum(float v) {
-#pragma unroll
-  for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
 }
 
 // ---- warp-level tensor-core helpers (mma.sync m16n8k8, TF32 inputs, FP32 accumulate) ----
@@ -284,57 +136,6 @@ __device__ __forceinline__ void mma3_tf32(float* d, const uint32_t* ah, const ui
   mma_tf32(d, al, bh);
   mma_tf32(d, ah, bl);
   mma_tf32(d, ah, bh);
-}
-
-// acc += sum_{e in [lo, hi)} val[e] * Xg[col[e], f0 .. f0+VEC).  `batches` must
-// be the same on every lane of the warp (the maximum over its teams).  The
-// (col, val) pairs of batch j+1 are fetched while the gathers of batch j are in
-// flight, so a batch costs one memory round trip.
-template <int KP, bool MIXED>
-__device__ __forceinline__ void gather(const int32_t* __restrict__ col, const void* __restrict__ valp,
-                                       const void* __restrict__ Xg, int64_t lo, int64_t hi, int batches,
-                                       int lt, int f0, float* acc) {
-  using L = Lay<KP>;
-  using VT = typename GatherT<MIXED>::V;
-  const VT* val = reinterpret_cast<const VT*>(valp);
-  int ci[L::PER];
-  float cv[L::PER];
-#pragma unroll
-  for (int p = 0; p < L::PER; ++p) {
-    const int64_t e = lo + lt + p * L::T;
-    const bool ok = batches > 0 && e < hi;
-    ci[p] = ok ? __ldg(col + e) : 0;
-    cv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
-  }
-  for (int j = 0; j < batches; ++j) {
-    float xv[L::NB][L::VEC];
-#pragma unroll
-    for (int u = 0; u < L::NB; ++u) {
-      const int c = L::T > 1 ? __shfl_sync(kFull, ci[u / L::T], u % L::T, L::T) : ci[u];
-      load_feat<L::VEC, MIXED>(Xg, (int64_t)c * KP + f0, xv[u]);
-    }
-    int ni[L::PER];
-    float nv[L::PER];
-    const int64_t e1 = lo + (int64_t)(j + 1) * L::NB;
-#pragma unroll
-    for (int p = 0; p < L::PER; ++p) {
-      const int64_t e = e1 + lt + p * L::T;
-      const bool ok = e < hi;
-      ni[p] = ok ? __ldg(col + e) : 0;
-      nv[p] = ok ? to_f(__ldg(val + e)) : 0.0f;
-    }
-#pragma unroll
-    for (int u = 0; u < L::NB; ++u) {
-      const float v = L::T > 1 ? __shfl_sync(kFull, cv[u / L::T], u % L::T, L::T) : cv[u];
-#pragma unroll
-      for (int q = 0; q < L::VEC; ++q) acc[q] = fmaf(v, xv[u][q], acc[q]);
-    }
-#pragma unroll
-    for (int p = 0; p < L::PER; ++p) {
-      ci[p] = ni[p];
-      cv[p] = nv[p];
-    }
-  }
 }
 
 // Euclidean projection of one row onto the unit simplex (the row's KP values
@@ -794,113 +595,6 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
   }
   extern __shared__ __align__(16) float smem[];
   pass_range<KP, MIXED, EVAL>(a, pass, p0, p1, blockIdx.x, smem);
-}
-
-// Split iteration, step 1: z_i = (S Xbar^{pass})_i for every row, stored in
-// Z_{(pass+1)&1}, plus the partial products of chunked rows.  Pure gather, no
-// per-tile barrier: warps take work units from a global counter (units of
-// TPW chunks first, then units of TPW * kRowsPerUnit consecutive positions of
-// the degree order, so the teams of a warp have equal trip counts).  Each
-// row's result is computed by exactly one team in a fixed order, so the
-// dynamic schedule does not change any value.
-constexpr int kRowsPerUnit = 4;
-
-// Work units of one instance's gather: chunk units, then row units.
-template <int KP>
-__host__ __device__ __forceinline__ int64_t spmm_chunk_units(int64_t n_chunks) {
-  return (n_chunks + Lay<KP>::TPW - 1) / Lay<KP>::TPW;
-}
-template <int KP>
-__host__ __device__ __forceinline__ int64_t spmm_units(int64_t n, int64_t n_heavy, int64_t n_chunks) {
-  const int64_t per = (int64_t)Lay<KP>::TPW * kRowsPerUnit;
-  return spmm_chunk_units<KP>(n_chunks) + (n - n_heavy + per - 1) / per;
-}
-
-// One warp processes gather unit u of an instance (see spmm_kernel).
-template <int KP, bool MIXED>
-__device__ __forceinline__ void spmm_unit(const PassArgs& a, int64_t pass, int64_t u, int lane) {
-  using L = Lay<KP>;
-  const float* P = (pass & 1) ? a.X1 : a.X0;
-  const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
-  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
-  const int tiw = lane / L::T, lt = lane % L::T, f0 = lt * L::VEC;
-  const int64_t n_cu = spmm_chunk_units<KP>(a.n_chunks);
-  if (u < n_cu) {
-    const int64_t c = u * L::TPW + tiw;
-    const bool act = c < a.n_chunks;
-    const int64_t lo = act ? a.chunk_e0[c] : 0, hi = act ? a.chunk_e1[c] : 0;
-    float acc[L::VEC];
-#pragma unroll
-    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-    const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
-    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
-    if (act) store_row<L::VEC>(a.hv_part + c * KP + f0, acc);
-    return;
-  }
-  const int64_t base = a.n_heavy + (u - n_cu) * L::TPW * kRowsPerUnit;
-  int64_t nrow = (base + tiw < a.n) ? (int64_t)a.order[base + tiw] : 0;
-#pragma unroll 1
-  for (int m = 0; m < kRowsPerUnit; ++m) {
-    const int64_t pos = base + (int64_t)m * L::TPW + tiw;
-    const bool act = pos < a.n;
-    const int64_t row = nrow;
-    const int64_t npos = pos + L::TPW;
-    nrow = (m + 1 < kRowsPerUnit && npos < a.n) ? (int64_t)a.order[npos] : 0;
-    const int64_t lo = act ? a.row_ptr[row] : 0, hi = act ? a.row_ptr[row + 1] : 0;
-    float acc[L::VEC];
-#pragma unroll
-    for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-    const int batches = __reduce_max_sync(kFull, (int)((hi - lo + L::NB - 1) / L::NB));
-    gather<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, f0, acc);
-    if (act) store_row<L::VEC>(Zc + row * KP + f0, acc);
-  }
-}
-
-template <int KP, bool MIXED>
-__global__ void __launch_bounds__(Lay<KP>::NT) spmm_kernel(PassArgs a) {
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
-  const int lane = threadIdx.x & 31;
-  const int64_t units = spmm_units<KP>(a.n, a.n_heavy, a.n_chunks);
-  for (;;) {
-    unsigned long long u = 0;
-    if (lane == 0) u = atomicAdd(a.work, 1ull);
-    u = __shfl_sync(kFull, u, 0);
-    if ((int64_t)u >= units) break;
-    spmm_unit<KP, MIXED>(a, pass, (int64_t)u, lane);
-  }
-}
-
-// Split iteration, step 2: z of every chunked row = sum of its chunk partials
-// in chunk order.
-template <int KP>
-__device__ __forceinline__ void finalize_row(const PassArgs& a, int64_t pass, int64_t p, int lt) {
-  using L = Lay<KP>;
-  float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
-  const int f0 = lt * L::VEC;
-  const int64_t row = a.order[p];
-  float acc[L::VEC];
-#pragma unroll
-  for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
-  for (int64_t c = a.chunk_ptr[p]; c < a.chunk_ptr[p + 1]; ++c) {
-    float pv[L::VEC];
-    load_row<L::VEC>(a.hv_part + c * KP + f0, pv);
-#pragma unroll
-    for (int q = 0; q < L::VEC; ++q) acc[q] += pv[q];
-  }
-  store_row<L::VEC>(Zc + row * KP + f0, acc);
-}
-
-template <int KP>
-__global__ void __launch_bounds__(256) heavy_finalize_kernel(PassArgs a) {
-  using L = Lay<KP>;
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t teams = (int64_t)gridDim.x * blockDim.x / L::T;
-  for (int64_t p = t / L::T; p < a.n_heavy; p += teams) finalize_row<KP>(a, pass, p, (int)(t % L::T));
 }
 
 // Split iteration, step 3: the row-local update (extrapolation, y G, step,
