@@ -231,6 +231,23 @@ CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, co
 CLUSTER_API cluster_status cluster_objective_static(const cluster_csr* S, int32_t k, const float* U,
                                                     void* stream, double* f);
 
+/* Second-order check (Sect. 4, Theorem 4.1, Eq. "hessian").  In row notation
+ * (U = Xbar^T, W = V^T) the Hessian of f at U applied to a direction W is
+ *     H[W] = -4 S W + 4 W (U^T U) + 4 U (U^T W + W^T U).
+ * The call computes, from one product S W on the device:
+ *   HW         (optional) H[W], n x k row-major float32, device;
+ *   curvature  (optional) <W, H[W]> in float64, host;
+ *   slope      (optional) <grad f(U), W> = <-4 (S U - U U^T U), W> in float64, host.
+ * A direction tangent to Omega at U has rows summing to zero (and w_ia >= 0
+ * where u_ia = 0); a stationary U with a tangent W of negative curvature is
+ * not a local minimum (the 0.5 J saddle of Example 4.1 has curvature -4 along
+ * the direction the paper prints).  U and W are n x k row-major float32 device
+ * arrays (not modified); S as for cluster_objective (symmetric).  The library
+ * allocates and frees its own scratch and synchronises `stream`.  Errors:
+ * EINVAL for NULL pointers or k outside [1, 128], ENOMEM, ECUDA. */
+CLUSTER_API cluster_status cluster_hessian_apply(const cluster_csr* S, int32_t k, const float* U, const float* W,
+                                                 void* stream, float* HW, double* curvature, double* slope);
+
 /* Checkpoint.  The state is everything a resumed run needs to continue bit
  * for bit: the two newest iterates, the stored product S*Xbar^{n-1}, the
  * float64 Gram matrices and scalars.  cluster_state_size gives the byte size;

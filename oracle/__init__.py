@@ -20,6 +20,9 @@ from .fista import (
     gradient_matrix,
     gradient_columns,
     hessian_apply,
+    hessian_apply_sparse,
+    curvature,
+    slope,
     duchi,
     project_omega,
     lipschitz,
@@ -34,6 +37,6 @@ from .fista import (
 
 __all__ = [
     "frob2", "objective_dense", "objective_trace", "gradient_matrix", "gradient_columns",
-    "hessian_apply", "duchi", "project_omega", "lipschitz", "gpa", "fista",
+    "hessian_apply", "hessian_apply_sparse", "curvature", "slope", "duchi", "project_omega", "lipschitz", "gpa", "fista",
     "OracleResult", "csr_from_edges", "spectral_norm", "momentum_factors", "fista_step_rows",
 ]

@@ -109,6 +109,28 @@ def hessian_apply(S, U, V) -> np.ndarray:
     return -4.0 * (Sd - U @ U.T) @ W + 4.0 * (W @ U.T + U @ W.T) @ U
 
 
+def hessian_apply_sparse(S, U, W) -> np.ndarray:
+    """The same operator as hessian_apply without forming N x N matrices:
+    (U U^T) W = U (U^T W), (W U^T) U = W (U^T U), (U W^T) U = U (W^T U), so
+    H[W] = -4 S W + 4 U (U^T W) + 4 W (U^T U) + 4 U (W^T U); S stays sparse."""
+    S = _as_csr(S)
+    U = np.asarray(U, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    return -4.0 * (S @ W) + 4.0 * U @ (U.T @ W) + 4.0 * W @ (U.T @ U) + 4.0 * U @ (W.T @ U)
+
+
+def curvature(S, U, W) -> float:
+    """<W, H[W]> (Theorem 4.1): negative along a tangent direction at a
+    stationary point means the point is not a local minimum (Sect. 4)."""
+    return float(np.sum(np.asarray(W, dtype=np.float64) * hessian_apply_sparse(S, U, W)))
+
+
+def slope(S, U, W) -> float:
+    """Directional derivative <grad f(U), W>, gradient in the column form of
+    Eq. "gradient_column" (sparse S)."""
+    return float(np.sum(np.asarray(W, dtype=np.float64) * gradient_columns(S, U)))
+
+
 # ----------------------------------------------------------------------------
 # projection onto the simplex (Algorithm 1) and onto Omega
 # ----------------------------------------------------------------------------

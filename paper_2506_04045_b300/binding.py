@@ -103,6 +103,9 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_double)]),
     "cluster_objective_static": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.c_int32, _P, _P,
                                                 ctypes.POINTER(ctypes.c_double)]),
+    "cluster_hessian_apply": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
     "cluster_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "cluster_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
@@ -449,6 +452,19 @@ def objective_static(row_ptr, col, val, U, stream=None) -> float:
     check(lib.cluster_objective_static(ctypes.byref(csr), int(U.shape[1]), _ptr(U), _stream_ptr(stream),
                                        ctypes.byref(f)))
     return f.value
+
+
+def hessian_apply(row_ptr, col, val, U, W, want_hw: bool = True, stream=None):
+    """Hessian of f at U applied to W through cluster_hessian_apply (device
+    tensors, n x k float32).  Returns (H[W] or None, <W, H[W]>, <grad f(U), W>)."""
+    import torch
+    lib = load()
+    csr = make_csr(row_ptr, col, val)
+    HW = torch.empty_like(U) if want_hw else None
+    curv, slope = ctypes.c_double(), ctypes.c_double()
+    check(lib.cluster_hessian_apply(ctypes.byref(csr), int(U.shape[1]), _ptr(U), _ptr(W), _stream_ptr(stream),
+                                    _ptr(HW) if HW is not None else None, ctypes.byref(curv), ctypes.byref(slope)))
+    return HW, curv.value, slope.value
 
 
 def csr_from_edges(n: int, src, dst, w=None, add_unit_diag: bool = True):

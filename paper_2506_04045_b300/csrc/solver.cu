@@ -15,6 +15,7 @@
 
 #include "init_kernels.cuh"
 #include "pass_kernels.cuh"
+#include "hessian_kernels.cuh"
 #include "solver_impl.h"
 #include "util.h"
 
@@ -1040,6 +1041,164 @@ extern "C" void cluster_destroy(cluster_ctx* c) {
 // ---------------------------------------------------------------------------
 // standalone objective
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// second-order check: H[W], <W, H[W]>, <grad f(U), W> from one product S W
+// ---------------------------------------------------------------------------
+template <int KP>
+static cluster_status hess_combine(cluster_ctx* c, const float* Up, const float* Wp, float* HW, double* curvature,
+                                   double* slope) {
+  constexpr int E2 = KP * KP;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int gparts = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n + kHessRows - 1) / kHessRows));
+  const int echunks = (3 * E2 + 256 * kHessPerThr - 1) / (256 * kHessPerThr);
+  float* gpart = nullptr;
+  double* gsum = nullptr;
+  float *Gf = nullptr, *Bf = nullptr;
+  double* dots = nullptr;
+  const int rparts = 4 * sms;
+  cluster_status st = CLUSTER_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaMalloc(&gpart, sizeof(float) * 3 * E2 * gparts)) != cudaSuccess ||
+        (e = cudaMalloc(&gsum, sizeof(double) * 3 * E2)) != cudaSuccess ||
+        (e = cudaMalloc(&Gf, sizeof(float) * 2 * E2)) != cudaSuccess ||
+        (e = cudaMalloc(&dots, sizeof(double) * 2 * rparts)) != cudaSuccess) {
+      set_error("hessian scratch: %s", cudaGetErrorString(e));
+      st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+      break;
+    }
+    Bf = Gf + E2;
+    hess_gram_kernel<KP><<<dim3(gparts, echunks), 256, 0, s>>>(Up, Wp, n, gpart);
+    hess_fold_kernel<<<(3 * E2 + 255) / 256, 256, 0, s>>>(gpart, gparts, 3 * E2, gsum);
+    std::vector<double> g(3 * E2);
+    cudaMemcpyAsync(g.data(), gsum, sizeof(double) * 3 * E2, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      set_error("hessian Grams: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+      break;
+    }
+    const double* G = g.data();
+    const double* M = G + E2;  // U^T W
+    const double* N = M + E2;  // W^T W
+    std::vector<float> gb(2 * E2);
+    double NG = 0.0, MM = 0.0, MMt = 0.0, MG = 0.0;
+    for (int a = 0; a < KP; ++a)
+      for (int b = 0; b < KP; ++b) {
+        gb[a * KP + b] = (float)G[a * KP + b];
+        gb[E2 + a * KP + b] = (float)(M[a * KP + b] + M[b * KP + a]);
+        NG += N[a * KP + b] * G[a * KP + b];
+        MM += M[a * KP + b] * M[a * KP + b];
+        MMt += M[a * KP + b] * M[b * KP + a];
+        MG += M[a * KP + b] * G[a * KP + b];
+      }
+    cudaMemcpyAsync(Gf, gb.data(), sizeof(float) * 2 * E2, cudaMemcpyHostToDevice, s);
+    const int smem = (int)(sizeof(float) * 2 * E2);
+    if ((e = cudaFuncSetAttribute(hess_row_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess) {
+      set_error("hessian attributes: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+      break;
+    }
+    hess_row_kernel<KP><<<rparts, 256, smem, s>>>(Up, Wp, c->Z[1], Gf, Bf, n, c->k, HW, dots);
+    std::vector<double> d(2 * rparts);
+    cudaMemcpyAsync(d.data(), dots, sizeof(double) * 2 * rparts, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      set_error("hessian rows: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+      break;
+    }
+    double wz = 0.0, uz = 0.0;
+    for (int p = 0; p < rparts; ++p) {
+      wz += d[2 * p];
+      uz += d[2 * p + 1];
+    }
+    // <W, H[W]> = -4 <W, S W> + 4 <W^T W, G> + 4 <M, M + M^T>;  <grad f, W> = -4 <U, S W> + 4 <M, G>
+    if (curvature) *curvature = -4.0 * wz + 4.0 * NG + 4.0 * (MM + MMt);
+    if (slope) *slope = -4.0 * uz + 4.0 * MG;
+  } while (0);
+  if (gpart) cudaFree(gpart);
+  if (gsum) cudaFree(gsum);
+  if (Gf) cudaFree(Gf);
+  if (dots) cudaFree(dots);
+  return st;
+}
+
+static cluster_status hessian_impl(const cluster_csr* S, int32_t k, const float* U, const float* W, void* stream,
+                                   float* HW, double* curvature, double* slope, cluster_ctx* c) {
+  c->stream = (cudaStream_t)stream;
+  c->n = S->n;
+  c->nnz = S->nnz;
+  c->k = k;
+  c->KP = padded_k(k);
+  c->mixed = false;
+  FC_CUDA(cudaGetDevice(&c->dev));
+  cudaStream_t s = c->stream;
+  FC_TRY(prepare_rowptr(S, s, &c->rp, &c->rp_owned));
+  c->col = S->col;
+  c->val = S->val;
+  FC_CUDA(kp_setup_attrs(c->KP));
+  int sms = 0;
+  FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int occ = kp_occupancy(c->KP, false);
+  const int R = kp_rows_per_tile(c->KP);
+  int64_t parts = (int64_t)sms * occ;
+  if (parts > (c->n + R - 1) / R) parts = (c->n + R - 1) / R;
+  c->parts = (int)std::max<int64_t>(1, parts);
+  c->heavy_grid = sms * occ;
+  c->heavy_H = std::max<int64_t>(64, 16384 / c->KP);
+  FC_TRY(build_schedule(c));
+  c->spmm_grid = sms * kp_occ_spmm(c->KP, false);
+  const size_t nk = (size_t)c->n * c->KP;
+  // X0 = W (the gathered operand), X1 = U; S W lands in Z1 (a pass-0 product)
+  FC_CUDA(cudaMalloc(&c->X[0], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->X[1], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->Z[1], sizeof(float) * nk));
+  FC_CUDA(cudaMalloc(&c->work, sizeof(unsigned long long)));
+  FC_CUDA(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), s));
+  FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
+  FistaState h;
+  memset(&h, 0, sizeof(h));
+  h.k = k;
+  h.limit = 1;  // one product: pass 0 of a state that is not done
+  FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(W, c->n, k, c->KP, c->X[0], nullptr, nullptr, nullptr);
+  pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U, c->n, k, c->KP, c->X[1], nullptr, nullptr, nullptr);
+  PassArgs a = make_pass_args(c, true);
+  kp_launch_spmm(c->KP, a, c->spmm_grid, false, s);
+  if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
+  FC_CUDA(cudaGetLastError());
+  cluster_status st = CLUSTER_OK;
+  switch (c->KP) {
+    case 2: st = hess_combine<2>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    case 4: st = hess_combine<4>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    case 8: st = hess_combine<8>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    case 16: st = hess_combine<16>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    case 32: st = hess_combine<32>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    case 64: st = hess_combine<64>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+    default: st = hess_combine<128>(c, c->X[1], c->X[0], HW, curvature, slope); break;
+  }
+  return st;
+}
+
+extern "C" cluster_status cluster_hessian_apply(const cluster_csr* S, int32_t k, const float* U, const float* W,
+                                                void* stream, float* HW, double* curvature, double* slope) {
+  clear_error();
+  FC_TRY(check_csr_args(S, k));
+  if (!U || !W) FC_EINVAL("NULL argument");
+  cluster_ctx* c = new (std::nothrow) cluster_ctx();
+  if (!c) {
+    set_error("out of host memory");
+    return CLUSTER_ENOMEM;
+  }
+  cluster_status st = hessian_impl(S, k, U, W, stream, HW, curvature, slope, c);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  ctx_free(c);
+  return st;
+}
+
 extern "C" cluster_status cluster_objective(const cluster_csr* S, int32_t k, const float* U, void* stream,
                                             double* f) {
   clear_error();

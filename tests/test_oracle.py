@@ -130,6 +130,31 @@ def test_hessian_finite_differences(n, k, seed):
     assert np.allclose(H, fd, rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("n,k,seed", [(8, 2, 0), (40, 5, 1), (120, 16, 2)])
+def test_sparse_hessian_equals_dense_operator(n, k, seed):
+    # the sparse grouping is the dense operator of Theorem 4.1 (itself pinned by
+    # finite differences above); curvature and slope are its scalar forms
+    rng = np.random.default_rng(seed)
+    S = _rand_sym_sparse(rng, n)
+    U = _rand_simplex(rng, n, k)
+    W = rng.standard_normal((n, k))
+    H = oracle.hessian_apply(S, U, W)
+    assert np.allclose(oracle.hessian_apply_sparse(S, U, W), H, rtol=1e-12, atol=1e-10)
+    assert abs(oracle.curvature(S, U, W) - float(np.sum(W * H))) <= 1e-10 * max(1.0, float(np.abs(W * H).sum()))
+    G = oracle.gradient_matrix(S, U)
+    assert abs(oracle.slope(S, U, W) - float(np.sum(W * G))) <= 1e-10 * max(1.0, float(np.abs(W * G).sum()))
+
+
+def test_toy_curvature_and_slope_functions():
+    # Sect. 4 after the table: curvature -4 and zero slope along the printed direction
+    g, _, _ = _toy()
+    S = _toy_S()
+    _, _, U3 = _scenario(g, "scenario3")
+    Vbar = np.array([[float(v) for v in r] for r in g["hessian"][0:2]]).T
+    assert oracle.curvature(S, U3, Vbar) == float(g["hessian"][2][1])
+    assert oracle.slope(S, U3, Vbar) == float(g["hessian"][3][1])
+
+
 def test_toy_second_order_value():
     g, _, _ = _toy()
     S = _toy_S()
