@@ -10,6 +10,8 @@ from .gen import (
     sbm_pairs,
     dcsbm_edges,
     two_cluster_er_edges,
+    two_cluster_graph,
+    second_row_start,
     assemble_csr,
     pair_weights,
     dirichlet_u0,
@@ -20,6 +22,6 @@ from .gen import (
 
 __all__ = [
     "hash_u64", "uniform01", "stream_key",
-    "sbm_pairs", "dcsbm_edges", "two_cluster_er_edges",
+    "sbm_pairs", "dcsbm_edges", "two_cluster_er_edges", "two_cluster_graph", "second_row_start",
     "assemble_csr", "pair_weights", "dirichlet_u0", "GraphSpec", "make_graph", "batch_specs",
 ]

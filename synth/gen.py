@@ -222,13 +222,42 @@ def two_cluster_er_edges(n1: int, n2: int, p1: float, p2: float, bridges: int, s
     return torch.cat(out_s), torch.cat(out_d)
 
 
+def two_cluster_graph(n1: int, n2: int, deg1: float, deg2: float, bridges: int, seed: int,
+                      device=None, weighted: bool = False):
+    """The paper's artificial graph (Sect. 5, "Artificial graph"): two
+    Erdos-Renyi clusters of n1 and n2 nodes with edge probabilities
+    deg1 / (n1 - 1) and deg2 / (n2 - 1), ``bridges`` random inter-cluster edges,
+    0/1 similarity (unless ``weighted``) with a unit diagonal.  The paper's run
+    uses n1 = 500,000, n2 = 250,000, deg1 = 1200, deg2 = 1600, 200 bridges.
+    The paper prunes nodes of degree 0; at these degrees none occurs (checked).
+    Returns (row_ptr, col, val, labels) with labels 0 on [0, n1), 1 after."""
+    n = n1 + n2
+    s, d = two_cluster_er_edges(n1, n2, deg1 / (n1 - 1), deg2 / (n2 - 1), bridges, seed, device=device)
+    rp, c, v = assemble_csr(n, s, d, seed, weighted=weighted)
+    if n > 0 and int((rp[1:] - rp[:-1]).min()) < 2:
+        raise ValueError("a node without edges: the paper's pruning would remove it")
+    labels = torch.zeros(n, dtype=torch.int64, device=rp.device)
+    labels[n1:] = 1
+    return rp, c, v, labels
+
+
+def second_row_start(n: int, k: int = 2, device=None) -> torch.Tensor:
+    """The artificial-graph experiment's start X^0: every article fully in the
+    second cluster (U0 = e_2 in every row)."""
+    U0 = torch.zeros((n, k), dtype=torch.float32, device=_dev(device))
+    U0[:, 1] = 1.0
+    return U0
+
+
 # ----------------------------------------------------------------------------
 # CSR assembly
 # ----------------------------------------------------------------------------
 def assemble_csr(n: int, src: torch.Tensor, dst: torch.Tensor, seed: int,
-                 max_chunk_entries: int = 1 << 29) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+                 max_chunk_entries: int = 1 << 29,
+                 weighted: bool = True) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
     """Symmetric CSR of the similarity matrix: for each edge {a, b} with a != b,
-    s_ab = s_ba = pair_weights(a, b); duplicates merge (equal weights); s_ii = 1.
+    s_ab = s_ba = pair_weights(a, b) (or 1 when ``weighted`` is false, the
+    paper's 0/1 citation similarity); duplicates merge (equal weights); s_ii = 1.
 
     Returns (row_ptr int64 [n+1], col int32 [nnz], val float32 [nnz]) on the
     device of ``src``.  Columns are sorted within each row.  Rows are built in
@@ -261,8 +290,11 @@ def assemble_csr(n: int, src: torch.Tensor, dst: torch.Tensor, seed: int,
         keys = torch.unique(keys, sorted=True)
         r = keys // n
         c = keys % n
-        w = pair_weights(r, c, n, seed)
-        w = torch.where(r == c, torch.ones_like(w), w)
+        if weighted:
+            w = pair_weights(r, c, n, seed)
+            w = torch.where(r == c, torch.ones_like(w), w)
+        else:
+            w = torch.ones(r.shape, dtype=torch.float32, device=dev)
         cols.append(c.to(torch.int32))
         vals.append(w)
         counts.append(torch.bincount(r - r0, minlength=r1 - r0))

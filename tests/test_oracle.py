@@ -12,6 +12,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle
+import synth
 from conftest import read_sections
 
 
@@ -367,3 +368,30 @@ def test_step_rows_reproduces_fista_iterations():
         got = oracle.fista_step_rows(S, hist[n - 1], hist[n - 2], betas[n - 1], tau, rows)
         assert np.allclose(got, hist[n][rows], rtol=0, atol=1e-13)
     assert betas[:2] == [0.0, 0.0] and 0 < betas[2] < betas[3] < 1
+
+
+def test_artificial_two_cluster_recovery():
+    # Sect. 5, Experiment 2: from X^0 with ones in the second row, both GPA and
+    # FISTA recover the two planted clusters in fewer than 10 iterations.  The
+    # graph is the paper's construction at reduced size; the step keeps the
+    # paper's 4 tau n = 1.5 (tau = 5e-7 at n = 750,000).
+    rp, c, v, labels = synth.two_cluster_graph(8000, 4000, 480.0, 640.0, 20, seed=6)
+    n = 12000
+    S = sp.csr_matrix((v.numpy().astype(np.float64), c.numpy(), rp.numpy()), shape=(n, n))
+    assert np.all(S.data == 1.0)
+    U0 = synth.second_row_start(n).numpy().astype(np.float64)
+    tau = 1.5 / (4 * n)
+    truth = labels.numpy()
+    for accel in (False, True):
+        r = oracle.fista(S, U0, tau, max_iter=9, stop="none", accel=accel)
+        lab = np.argmax(r.U, axis=1)
+        agree = float((lab == truth).mean())
+        assert max(agree, 1.0 - agree) == 1.0, (accel, agree)
+        # first step in closed form: from rows e_2, U^T U = diag(0, n) and (S U)_i =
+        # (0, d_i) with d_i the row sum of S, so grad_i = (0, 4 (n - d_i)) and the
+        # projection of (0, 1 - 4 tau (n - d_i)) is (2 tau (n - d_i), 1 - 2 tau (n - d_i))
+        r1 = oracle.fista(S, U0, tau, max_iter=1, stop="none", accel=accel)
+        d = np.asarray(S.sum(axis=1)).ravel()
+        x1 = 2.0 * tau * (n - d)
+        assert np.allclose(r1.U, np.stack([x1, 1.0 - x1], axis=1), rtol=0, atol=1e-12)
+
