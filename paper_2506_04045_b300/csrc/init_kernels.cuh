@@ -119,6 +119,20 @@ static __global__ void degree_kernel(const int64_t* __restrict__ rp, int64_t n, 
   }
 }
 
+// key[p] = order[p] / chunk (the row chunk of the row at position p)
+static __global__ void chunk_key_kernel(const int32_t* __restrict__ order, int64_t m, int32_t chunk,
+                                        uint32_t* __restrict__ key) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+    key[p] = (uint32_t)(order[p] / chunk);
+}
+
+// sdeg[p] = deg[order[p]]
+static __global__ void gather_deg_kernel(const uint32_t* __restrict__ deg, const int32_t* __restrict__ order,
+                                         int64_t n, uint32_t* __restrict__ sdeg) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    sdeg[p] = deg[order[p]];
+}
+
 static __global__ void count_above_kernel(const uint32_t* __restrict__ deg, int64_t n, uint32_t thr,
                                    unsigned long long* cnt) {
   unsigned long long c = 0;

@@ -18,6 +18,7 @@
 #include "hessian_kernels.cuh"
 #include "solver_impl.h"
 #include "util.h"
+#include "schedule.cuh"
 
 namespace fc {
 
@@ -39,7 +40,7 @@ static int padded_k(int k) {
   return kp;
 }
 
-int grid_for(int64_t work, int threads = 256) {
+int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > 65535LL * 8) b = 65535LL * 8;
@@ -330,93 +331,6 @@ void fill_report(const cluster_ctx* c, cluster_report* rep) {
   rep->out_iter = s.out_iter;
   rep->done = s.done;
   rep->status = s.status;
-}
-
-static cluster_status build_schedule(cluster_ctx* c) {
-  const int64_t n = c->n;
-  cudaStream_t s = c->stream;
-  uint32_t *deg = nullptr, *sdeg = nullptr;
-  int32_t* iota = nullptr;
-  void* tmp = nullptr;
-  size_t tmp_bytes = 0, tmp2 = 0;
-  int64_t *cost = nullptr, *prefix = nullptr, *hlo = nullptr;
-  unsigned long long* cnt = nullptr;
-  cluster_status st = CLUSTER_OK;
-  auto fail = [&](cudaError_t e, const char* what) {
-    set_error("%s: %s", what, cudaGetErrorString(e));
-    st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
-  };
-  cudaError_t e;
-  do {
-    if ((e = cudaMalloc(&deg, sizeof(uint32_t) * n)) != cudaSuccess) { fail(e, "alloc deg"); break; }
-    if ((e = cudaMalloc(&sdeg, sizeof(uint32_t) * n)) != cudaSuccess) { fail(e, "alloc sdeg"); break; }
-    if ((e = cudaMalloc(&iota, sizeof(int32_t) * n)) != cudaSuccess) { fail(e, "alloc iota"); break; }
-    if ((e = cudaMalloc(&c->order, sizeof(int32_t) * n)) != cudaSuccess) { fail(e, "alloc order"); break; }
-    degree_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, n, deg, iota);
-    // rows by degree, descending (stable radix sort: deterministic)
-    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, deg, sdeg, iota, c->order, (int)n, 0, 32, s);
-    if ((e = cudaMalloc(&cost, sizeof(int64_t) * n)) != cudaSuccess) { fail(e, "alloc cost"); break; }
-    if ((e = cudaMalloc(&prefix, sizeof(int64_t) * n)) != cudaSuccess) { fail(e, "alloc prefix"); break; }
-    cub::DeviceScan::InclusiveSum(nullptr, tmp2, cost, prefix, (int)n, s);
-    if (tmp2 > tmp_bytes) tmp_bytes = tmp2;
-    if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) { fail(e, "alloc sort temp"); break; }
-    if ((e = cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, sdeg, iota, c->order, (int)n, 0, 32,
-                                                       s)) != cudaSuccess) {
-      fail(e, "degree sort");
-      break;
-    }
-    // chunked ("heavy") rows: degree above H, split into chunks of H nonzeros
-    if ((e = cudaMalloc(&cnt, sizeof(unsigned long long))) != cudaSuccess) { fail(e, "alloc cnt"); break; }
-    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
-    count_above_kernel<<<grid_for(n), 256, 0, s>>>(sdeg, n, (uint32_t)c->heavy_H, cnt);
-    unsigned long long nh = 0;
-    cudaMemcpyAsync(&nh, cnt, sizeof(nh), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "degree schedule"); break; }
-    c->n_heavy = (int64_t)nh;
-    if (nh > 0) {
-      std::vector<uint32_t> hdeg(nh);
-      std::vector<int64_t> hlo_h(nh);
-      if ((e = cudaMalloc(&hlo, sizeof(int64_t) * nh)) != cudaSuccess) { fail(e, "alloc hlo"); break; }
-      heavy_lo_kernel<<<grid_for((int64_t)nh), 256, 0, s>>>(c->rp, c->order, (int64_t)nh, hlo);
-      cudaMemcpyAsync(hdeg.data(), sdeg, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(hlo_h.data(), hlo, sizeof(int64_t) * nh, cudaMemcpyDeviceToHost, s);
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "heavy rows"); break; }
-      std::vector<int64_t> cptr(nh + 1), ce0, ce1;
-      cptr[0] = 0;
-      for (size_t p = 0; p < nh; ++p) {
-        const int64_t d = hdeg[p];
-        for (int64_t o = 0; o < d; o += c->heavy_H) {
-          ce0.push_back(hlo_h[p] + o);
-          ce1.push_back(hlo_h[p] + std::min<int64_t>(d, o + c->heavy_H));
-        }
-        cptr[p + 1] = (int64_t)ce0.size();
-        c->heavy_nnz += d;
-      }
-      c->n_chunks = (int64_t)ce0.size();
-      if ((e = cudaMalloc(&c->chunk_ptr, sizeof(int64_t) * (nh + 1))) != cudaSuccess) { fail(e, "alloc chunks"); break; }
-      if ((e = cudaMalloc(&c->chunk_e0, sizeof(int64_t) * c->n_chunks)) != cudaSuccess) { fail(e, "alloc chunks"); break; }
-      if ((e = cudaMalloc(&c->chunk_e1, sizeof(int64_t) * c->n_chunks)) != cudaSuccess) { fail(e, "alloc chunks"); break; }
-      if ((e = cudaMalloc(&c->hv_part, sizeof(float) * c->n_chunks * c->KP)) != cudaSuccess) { fail(e, "alloc hv"); break; }
-      cudaMemcpyAsync(c->chunk_ptr, cptr.data(), sizeof(int64_t) * (nh + 1), cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(c->chunk_e0, ce0.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(c->chunk_e1, ce1.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice, s);
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "upload chunks"); break; }
-    }
-    // cost-balanced position ranges, one per block
-    cost_kernel<<<grid_for(n), 256, 0, s>>>(sdeg, n, c->n_heavy, (uint32_t)c->heavy_H, c->row_cost, cost);
-    if ((e = cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, cost, prefix, (int)n, s)) != cudaSuccess) {
-      fail(e, "cost scan");
-      break;
-    }
-    if ((e = cudaMalloc(&c->cta_pos, sizeof(int64_t) * (c->parts + 1))) != cudaSuccess) { fail(e, "alloc cta_pos"); break; }
-    partition_kernel<<<(c->parts + 1 + 255) / 256, 256, 0, s>>>(prefix, n, c->parts, c->cta_pos);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "partition"); break; }
-    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "schedule kernels"); break; }
-  } while (0);
-  void* tmps[] = {deg, sdeg, iota, tmp, cost, prefix, hlo, cnt};
-  for (void* p : tmps)
-    if (p) cudaFree(p);
-  return st;
 }
 
 static cluster_status power_norm(cluster_ctx* c, double* out) {

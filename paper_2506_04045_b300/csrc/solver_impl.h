@@ -68,7 +68,7 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init);
 cluster_status read_state(cluster_ctx* c);
 void fill_report(const cluster_ctx* c, cluster_report* rep);
 cluster_status finalize_loss(cluster_ctx* c);  // make the report's f the loss of the output iterate
-int grid_for(int64_t work, int threads);
+int grid_for(int64_t work, int threads = 256);
 
 // Non-owning batch over instances owned by the caller (batch.cu).
 cluster_status batch_view_new(void* stream, int graph_chunk, cluster_batch** out);
