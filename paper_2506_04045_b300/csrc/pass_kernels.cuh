@@ -138,6 +138,15 @@ __device__ __forceinline__ void mma3_tf32(float* d, const uint32_t* ah, const ui
   mma_tf32(d, ah, bh);
 }
 
+// hi + lo += x with the rounding error of the add kept in lo (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+
 // Euclidean projection of one row onto the unit simplex (the row's KP values
 // spread over the T lanes of a team, VEC per lane; features >= k are padding).
 // Michelot's active-set iteration: theta = (sum_{a in A} v_a - 1) / |A|, then
@@ -157,7 +166,9 @@ __device__ __forceinline__ void project_simplex(const float* v, float* x, int f0
   }
   s = team_sum<L::T>(s);
   c = team_sum<L::T>(c);
-  float theta = (s - 1.0f) / c;
+  // c counts at most KP entries; the approximate quotient (2 ulp) is ample for
+  // a threshold that only needs float32 accuracy
+  float theta = __fdividef(s - 1.0f, c);
   for (int it = 0; it <= KP; ++it) {
     float s2 = 0.f, c2 = 0.f;
 #pragma unroll
@@ -172,7 +183,7 @@ __device__ __forceinline__ void project_simplex(const float* v, float* x, int f0
     if (changed) {
       s = s2;
       c = c2;
-      theta = (s - 1.0f) / c;
+      theta = __fdividef(s - 1.0f, c);
     }
     if (!__any_sync(kFull, changed)) break;
   }
@@ -287,7 +298,10 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
 #pragma unroll
     for (int q = 0; q < BS * BS; ++q) gacc[j][q] = 0.f;
 
-  double tr_acc = 0.0, pg_acc = 0.0;
+  // running sums of the trace and PG terms over this range's rows as unevaluated
+  // float pairs (hi + lo, TwoSum), folded into float64 once at the end: the
+  // float64 pipe of this part is narrow
+  float tr_hi = 0.f, tr_lo = 0.f, pg_hi = 0.f, pg_lo = 0.f;
   int bad = 0;
 
   const int32_t* order = SPLIT ? nullptr : a.order;
@@ -338,7 +352,7 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
 #pragma unroll
     for (int q = 0; q < L::VEC; ++q) d = fmaf(pv[q], acc[q], d);
     d = team_sum<L::T>(d);
-    if (active && lt == 0) tr_acc += (double)d;
+    if (active && lt == 0) two_sum_acc(tr_hi, tr_lo, d);
 
     if constexpr (!EVAL) {
       float y[L::VEC], sy[L::VEC];
@@ -401,7 +415,7 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
         if (!isfinite(x[q]) || !isfinite(acc[q])) bad = 1;
       }
       pg = team_sum<L::T>(pg);
-      if (active && lt == 0) pg_acc += (double)pg;
+      if (active && lt == 0) two_sum_acc(pg_hi, pg_lo, pg);
       if (active) {
         store_row<L::VEC>(Q + row * KP + f0, x);
         if constexpr (!SPLIT) store_row<L::VEC>(a.Zp + row * KP + f0, acc);
@@ -488,6 +502,7 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
 
   // ---- block reductions (fixed order => bit-reproducible) ----
   double* dred = reinterpret_cast<double*>(xn_t);  // reuse tile memory
+  double tr_acc = (double)tr_hi + (double)tr_lo, pg_acc = (double)pg_hi + (double)pg_lo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     tr_acc += __shfl_down_sync(kFull, tr_acc, o);
