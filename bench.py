@@ -78,6 +78,49 @@ def dist_env():
     return ws, rank, local
 
 
+class Ranks:
+    """The run's ranks (one process per GPU, launched by torchrun): barrier,
+    max and sum over ranks.  A world of one when WORLD_SIZE is 1 (no process
+    group).  `backend`/`device` are nccl/cuda on GPUs; gloo/cpu in the
+    multi-process tests."""
+
+    def __init__(self, ws: int, backend: str = "nccl", device: str = "cuda"):
+        self.ws, self.device, self.dist = ws, device, None
+        if ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op: str) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=getattr(self.dist.ReduceOp, op))
+        return float(t.item())
+
+    def max(self, x) -> float:
+        return self._reduce(x, "MAX")
+
+    def sum(self, x) -> float:
+        return self._reduce(x, "SUM")
+
+    def weak_throughput(self, units, seconds):
+        """This rank processed `units` in `seconds`: returns (the slowest rank's
+        seconds, all ranks' units / that time), the whole-job figure."""
+        t = self.max(seconds)
+        return t, self.sum(units) / t
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -276,21 +319,8 @@ def run_native(args, ws, rank, local):
     import paper_2506_04045_b300 as pkg
 
     torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(ws)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     pkg.load()
     seed = args.seed + rank
@@ -379,7 +409,8 @@ def run_native(args, ws, rank, local):
         except Exception as exc:
             cpu = {"value": None, "unit": UNIT, "kind": "oracle", "error": str(exc)[:200]}
 
-    value = sum_over_ranks(dist, r["it_s"] if ws == 1 else K / (r["ms_total"] / 1000.0), ws)
+    # r["ms_total"] is already the slowest rank's time: whole-job iterations / that time
+    _, value = ranks.weak_throughput(K, r["ms_total"] / 1000.0)
     eq = None
     if "fp32" in res and "mixed" in res:
         eq = res["mixed"]["f"] <= res["fp32"]["f"] * (1 + 1e-5)
@@ -406,17 +437,7 @@ def run_native(args, ws, rank, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
-
-
-def sum_over_ranks(dist, x, ws):
-    if dist is None or ws == 1:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    ranks.close()
 
 
 def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
@@ -469,6 +490,7 @@ def run_batch(args, ws, rank, local):
     import synth
     import paper_2506_04045_b300 as pkg
     torch.cuda.set_device(local)
+    ranks = Ranks(ws)
     pkg.load()
     specs = synth.batch_specs(args.instances, seed=3 + 1000 * rank)
     t0 = time.perf_counter()
@@ -495,6 +517,7 @@ def run_batch(args, ws, rank, local):
         desc = b.autotune(trials=1)
         b.step(W)
         torch.cuda.synchronize()
+        ranks.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(torch.cuda.current_device()) as cs:
@@ -502,10 +525,12 @@ def run_batch(args, ws, rank, local):
             b.enqueue(K)
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ranks.barrier()
+        ms, inst_it_s = ranks.weak_throughput(len(inst) * K, e0.elapsed_time(e1) / 1000.0)
+        ms *= 1000.0
         reps = b.step(0)
         bytes_iter = sum(alg_bytes(sp.n, int(c.numel()), sp.k, mixed) for sp, (rp, c, v, U0) in zip(specs, inst))
-        res[form] = {"ms": ms, "inst_it_s": len(inst) * K / (ms / 1000.0), "desc": desc, "init_s": init_s,
+        res[form] = {"ms": ms, "inst_it_s": inst_it_s, "desc": desc, "init_s": init_s,
                      "bytes_iter": bytes_iter, "clocks": cs.summary(),
                      "iters_min": min(r["iters"] for r in reps), "iters_max": max(r["iters"] for r in reps)}
         b.close()
@@ -529,6 +554,7 @@ def run_batch(args, ws, rank, local):
             "clocks": r["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def run_er2(args, ws, rank, local):
@@ -546,6 +572,7 @@ def run_er2(args, ws, rank, local):
     import synth
     import paper_2506_04045_b300 as pkg
     torch.cuda.set_device(local)
+    ranks = Ranks(ws)
     pkg.load()
     n1, n2, d1, d2, bridges, tau = 500_000, 250_000, 1200.0, 1600.0, 200, 5e-7
     t0 = time.perf_counter()
@@ -574,6 +601,7 @@ def run_er2(args, ws, rank, local):
                 acc.append(round(max(a, 1.0 - a), 6))
             s.step(W)
             torch.cuda.synchronize()
+            ranks.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             with ClockSampler(torch.cuda.current_device()) as cs:
@@ -581,9 +609,11 @@ def run_er2(args, ws, rank, local):
                 kt = s.enqueue_profiled(K)
                 e1.record(stream)
                 torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
+            ranks.barrier()
+            secs, it_s = ranks.weak_throughput(K, e0.elapsed_time(e1) / 1000.0)
+            ms = secs * 1000.0
             first = next((i + 1 for i, a in enumerate(acc) if a >= 0.999), None)
-            res[name] = {"it_s": K / (ms / 1000.0), "ms_per_step": ms / K, "pass_ms": kt["pass_ms"],
+            res[name] = {"it_s": it_s, "ms_per_step": ms / K, "pass_ms": kt["pass_ms"],
                          "update_ms": kt["update_ms"], "fold_ms": kt["fold_ms"], "accuracy_by_iter": acc,
                          "first_iter_99_9": first, "clocks": cs.summary()}
             s.close()
@@ -609,6 +639,7 @@ def run_er2(args, ws, rank, local):
             "clocks": head["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def run_serve(args, ws, rank, local):
