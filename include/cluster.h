@@ -119,6 +119,13 @@ typedef struct cluster_options {
   int32_t fused_pass;  /* 0 = split iteration (gather kernel + streaming update
                           kernel, default); 1 = one fused kernel per iteration.
                           Same arithmetic; the Gram partial order differs.      */
+  int32_t relabel;     /* 1 = number the articles internally by decreasing
+                          degree (default): rows of frequently gathered articles
+                          then share cache lines and DRAM pages; inputs and
+                          outputs keep the caller's numbering, each row's sum
+                          keeps its order, only the Gram partial order differs.
+                          0 = keep the caller's numbering.                      */
+  int32_t _pad;
 } cluster_options;
 
 /* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("accel", ctypes.c_int32), ("borrow", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
-                ("graph_chunk", ctypes.c_int32), ("fused_pass", ctypes.c_int32)]
+                ("graph_chunk", ctypes.c_int32), ("fused_pass", ctypes.c_int32), ("relabel", ctypes.c_int32),
+                ("_pad", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

@@ -181,6 +181,64 @@ static __global__ void partition_kernel(const int64_t* __restrict__ prefix, int6
   cta_pos[c] = lo;
 }
 
+// ---- internal numbering by decreasing degree ----
+// inv[perm[p]] = p
+static __global__ void inverse_perm_kernel(const int32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ inv) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    inv[perm[p]] = (int32_t)p;
+}
+
+// cnt[p] = nonzeros of the caller's row perm[p]; cnt[n] = 0 (exclusive scan -> row pointers)
+static __global__ void permuted_count_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ perm,
+                                             int64_t n, int64_t* __restrict__ cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x)
+    cnt[p] = p < n ? rp[perm[p] + 1] - rp[perm[p]] : 0;
+}
+
+// One warp per internal row p: the caller's row perm[p], entries in their
+// order, columns renamed through inv.
+static __global__ void relabel_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                           const float* __restrict__ val, const int32_t* __restrict__ perm,
+                                           const int32_t* __restrict__ inv, const int64_t* __restrict__ rp2,
+                                           int64_t n, int32_t* __restrict__ col2, float* __restrict__ val2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; p < n; p += warps) {
+    const int64_t lo = rp[perm[p]], len = rp[perm[p] + 1] - lo, dst = rp2[p];
+    for (int64_t e = lane; e < len; e += 32) {
+      col2[dst + e] = inv[col[lo + e]];
+      val2[dst + e] = val[lo + e];
+    }
+  }
+}
+
+// X[p] = U[perm[p]] zero-padded to KP (+ optional copies)
+static __global__ void pad_perm_kernel(const float* __restrict__ U, const int32_t* __restrict__ perm, int64_t n,
+                                       int k, int KP, float* __restrict__ X, float* __restrict__ X2,
+                                       __nv_bfloat16* __restrict__ XS, __nv_bfloat16* __restrict__ XS2) {
+  const int64_t tot = n * KP;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / KP;
+    const int a = (int)(i % KP);
+    const float v = a < k ? U[(int64_t)perm[r] * k + a] : 0.0f;
+    X[i] = v;
+    if (X2) X2[i] = v;
+    if (XS) XS[i] = __float2bfloat16_rn(v);
+    if (XS2) XS2[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// U[i] = X[inv[i]] without the padding
+static __global__ void unpad_perm_kernel(const float* __restrict__ X, const int32_t* __restrict__ inv, int64_t n,
+                                         int k, int KP, float* __restrict__ U) {
+  const int64_t tot = n * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / k;
+    const int a = (int)(i % k);
+    U[i] = X[(int64_t)inv[r] * KP + a];
+  }
+}
+
 // n x k (row-major, stride k) -> n x KP zero-padded float32 (+ optional copies)
 static __global__ void pad_kernel(const float* __restrict__ U, int64_t n, int k, int KP, float* __restrict__ X,
                            float* __restrict__ X2, __nv_bfloat16* __restrict__ XS,

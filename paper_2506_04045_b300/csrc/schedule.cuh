@@ -1,7 +1,8 @@
-// Row schedule of a solver context: the processing order of the gather
-// (hub rows first in degree order, then chunks of consecutive rows, degree
-// order inside each chunk), the chunk table of hub rows and the cost-balanced
-// position ranges of the fused pass.  Included by solver.cu only.
+// Row schedule of a solver context: the internal numbering of the articles
+// (by decreasing degree), the processing order of the gather (hub rows first
+// in degree order, then chunks of consecutive rows, degree order inside each
+// chunk), the chunk table of hub rows and the cost-balanced position ranges
+// of the fused pass.  Included by solver.cu only.
 #pragma once
 #include <cub/cub.cuh>
 
@@ -19,6 +20,37 @@ namespace fc {
 #define FC_ROW_CHUNK 8192
 #endif
 static const int32_t kRowChunk = FC_ROW_CHUNK;
+
+// perm = rows by decreasing degree (stable radix sort: deterministic)
+static cluster_status degree_order(cluster_ctx* c, int32_t* perm) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  uint32_t *deg = nullptr, *sdeg = nullptr;
+  int32_t* iota = nullptr;
+  void* tmp = nullptr;
+  size_t tb = 0;
+  cluster_status st = CLUSTER_OK;
+  cudaError_t e;
+  cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, deg, sdeg, iota, perm, (int)n, 0, 32, s);
+  if ((e = cudaMalloc(&deg, sizeof(uint32_t) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&sdeg, sizeof(uint32_t) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&iota, sizeof(int32_t) * n)) != cudaSuccess || (e = cudaMalloc(&tmp, tb)) != cudaSuccess) {
+    set_error("degree order: %s", cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+  } else {
+    degree_kernel<<<grid_for(n), 256, 0, s>>>(c->rp, n, deg, iota);
+    if ((e = cub::DeviceRadixSort::SortPairsDescending(tmp, tb, deg, sdeg, iota, perm, (int)n, 0, 32, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      set_error("degree order: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+    }
+  }
+  void* fr[] = {deg, sdeg, iota, tmp};
+  for (void* q : fr)
+    if (q) cudaFree(q);
+  return st;
+}
 
 static cluster_status build_schedule(cluster_ctx* c) {
   const int64_t n = c->n;
@@ -136,6 +168,67 @@ static cluster_status build_schedule(cluster_ctx* c) {
   for (void* p : tmps)
     if (p) cudaFree(p);
   return st;
+}
+
+// Internal numbering by decreasing degree (stable): internal row p is the
+// caller's row perm[p].  The context keeps its own relabelled copy of S (row
+// pointers, renamed columns, values; each row's entries in their original
+// order, so every row's sum is unchanged) and frees any copy it owned before.
+static cluster_status relabel_csr(cluster_ctx* c) {
+  const int64_t n = c->n, nnz = c->nnz;
+  cudaStream_t s = c->stream;
+  FC_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * n));
+  FC_CUDA(cudaMalloc(&c->inv, sizeof(int32_t) * n));
+  FC_TRY(degree_order(c, c->perm));
+  inverse_perm_kernel<<<grid_for(n), 256, 0, s>>>(c->perm, n, c->inv);
+  int64_t *cnt = nullptr, *rp2 = nullptr;
+  int32_t* col2 = nullptr;
+  float* val2 = nullptr;
+  void* tmp = nullptr;
+  size_t tb = 0;
+  cluster_status st = CLUSTER_OK;
+  do {
+    cudaError_t e;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, rp2, (int)(n + 1), s);
+    if ((e = cudaMalloc(&cnt, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&rp2, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&col2, sizeof(int32_t) * std::max<int64_t>(1, nnz))) != cudaSuccess ||
+        (e = cudaMalloc(&val2, sizeof(float) * std::max<int64_t>(1, nnz))) != cudaSuccess ||
+        (e = cudaMalloc(&tmp, tb)) != cudaSuccess) {
+      set_error("relabel: %s", cudaGetErrorString(e));
+      st = e == cudaErrorMemoryAllocation ? CLUSTER_ENOMEM : CLUSTER_ECUDA;
+      break;
+    }
+    permuted_count_kernel<<<grid_for(n + 1), 256, 0, s>>>(c->rp, c->perm, n, cnt);
+    if ((e = cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, rp2, (int)(n + 1), s)) != cudaSuccess) {
+      set_error("relabel scan: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+      break;
+    }
+    relabel_rows_kernel<<<grid_for(n * 32), 256, 0, s>>>(c->rp, c->col, c->val, c->perm, c->inv, rp2, n, col2,
+                                                          val2);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
+      set_error("relabel: %s", cudaGetErrorString(e));
+      st = CLUSTER_ECUDA;
+      break;
+    }
+  } while (0);
+  if (cnt) cudaFree(cnt);
+  if (tmp) cudaFree(tmp);
+  if (st != CLUSTER_OK) {
+    if (rp2) cudaFree(rp2);
+    if (col2) cudaFree(col2);
+    if (val2) cudaFree(val2);
+    return st;
+  }
+  void* old[] = {c->rp_owned, c->col_owned, c->val_owned};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  c->rp = c->rp_owned = rp2;
+  c->col = c->col_owned = col2;
+  c->val = c->val_owned = val2;
+  c->relabeled = true;
+  return CLUSTER_OK;
 }
 
 }  // namespace fc

@@ -200,8 +200,7 @@ static cluster_status harvest(Request* r, cudaStream_t s) {
   fill_report(c, &r->rep);
   float* d_U = nullptr;
   FC_CUDA(cudaMalloc(&d_U, sizeof(float) * c->n * c->k));
-  const float* X = c->X[c->host_st.out_iter & 1];
-  unpad_kernel<<<grid_for(c->n * c->k, 256), 256, 0, s>>>(X, c->n, c->k, c->KP, d_U);
+  unpad_output(c, c->X[c->host_st.out_iter & 1], d_U, s);
   r->U.resize((size_t)c->n * c->k);
   cudaError_t e = cudaMemcpyAsync(r->U.data(), d_U, sizeof(float) * r->U.size(), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -234,7 +234,7 @@ void ctx_free(cluster_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
-                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work};
+                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work, c->perm, c->inv};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -447,6 +447,11 @@ static cluster_status sum_squares(const float* val, int64_t nnz, cudaStream_t s,
   return CLUSTER_OK;
 }
 
+void unpad_output(const cluster_ctx* c, const float* X, float* U_out, cudaStream_t s) {
+  if (c->relabeled) unpad_perm_kernel<<<grid_for(c->n * c->k), 256, 0, s>>>(X, c->inv, c->n, c->k, c->KP, U_out);
+  else unpad_kernel<<<grid_for(c->n * c->k), 256, 0, s>>>(X, c->n, c->k, c->KP, U_out);
+}
+
 cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const cluster_options* optp,
                          void* stream, cluster_ctx* c, bool capture) {
   FC_TRY(check_csr_args(S, k));
@@ -495,6 +500,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     c->val = c->val_owned;
   }
   if (opt.validate >= 1) FC_TRY(validate_inputs(c, U0));
+  if (opt.relabel && n > 1) FC_TRY(relabel_csr(c));
 
   // ||S||_F^2 in float64, step size
   double S2 = 0.0;
@@ -570,7 +576,11 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
 
   // Xbar^0 = U0 in buffer 0; buffer 1 starts as a copy (momentum is 0 for the first two passes)
-  pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U0, n, k, c->KP, c->X[0], c->X[1], c->XS[0], c->XS[1]);
+  if (c->relabeled)
+    pad_perm_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U0, c->perm, n, k, c->KP, c->X[0], c->X[1], c->XS[0],
+                                                          c->XS[1]);
+  else
+    pad_kernel<<<grid_for((int64_t)nk), 256, 0, s>>>(U0, n, k, c->KP, c->X[0], c->X[1], c->XS[0], c->XS[1]);
   FistaState& h = c->host_st;
   memset(&h, 0, sizeof(h));
   h.S2 = S2;
@@ -704,6 +714,7 @@ extern "C" void cluster_options_default(cluster_options* opt) {
   opt->max_iter = 1000;
   opt->graph_chunk = 16;
   opt->fused_pass = 0;
+  opt->relabel = 1;
 }
 
 extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
@@ -849,8 +860,7 @@ extern "C" cluster_status cluster_get_U(cluster_ctx* c, float* U_out) {
   if (!c || !U_out) FC_EINVAL("NULL argument");
   FC_CUDA(cudaSetDevice(c->dev));
   FC_TRY(read_state(c));
-  const float* X = c->X[c->host_st.out_iter & 1];
-  unpad_kernel<<<grid_for(c->n * c->k), 256, 0, c->stream>>>(X, c->n, c->k, c->KP, U_out);
+  unpad_output(c, c->X[c->host_st.out_iter & 1], U_out, c->stream);
   FC_CUDA(cudaGetLastError());
   FC_CUDA(cudaStreamSynchronize(c->stream));
   return CLUSTER_OK;
@@ -869,7 +879,7 @@ extern "C" cluster_status cluster_get_state(cluster_ctx* c, void* buf, size_t by
   if (bytes < state_bytes(c)) FC_EINVAL("state buffer too small (%zu < %zu)", bytes, state_bytes(c));
   FC_CUDA(cudaSetDevice(c->dev));
   char* p = (char*)buf;
-  StateHeader hd{kStateMagic, c->n, c->k, c->KP, c->mixed ? 1 : 0, c->split ? 1 : 0};
+  StateHeader hd{kStateMagic, c->n, c->k, c->KP, c->mixed ? 1 : 0, (c->split ? 1 : 0) | (c->relabeled ? 2 : 0)};
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
   const size_t e2 = (size_t)c->KP * c->KP, nk = (size_t)c->n * c->KP;
@@ -909,8 +919,8 @@ extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, siz
   StateHeader hd;
   memcpy(&hd, p, sizeof(hd));
   if (hd.magic != kStateMagic || hd.n != c->n || hd.k != c->k || hd.KP != c->KP || hd.mixed != (c->mixed ? 1 : 0) ||
-      hd.pad != (c->split ? 1 : 0))
-    FC_EINVAL("state does not match this context (n, k, precision or iteration form differ)");
+      hd.pad != ((c->split ? 1 : 0) | (c->relabeled ? 2 : 0)))
+    FC_EINVAL("state does not match this context (n, k, precision, iteration form or numbering differ)");
   p += sizeof(hd);
   FistaState fs;
   memcpy(&fs, p, sizeof(fs));

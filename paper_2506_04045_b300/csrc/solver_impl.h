@@ -26,6 +26,11 @@ struct cluster_ctx {
   int32_t* col_owned = nullptr;
   float* val_owned = nullptr;
   __nv_bfloat16* val16 = nullptr;
+  // internal numbering (opt.relabel): internal row p is the caller's row
+  // perm[p]; inv is the inverse (caller's row i -> internal row inv[i])
+  bool relabeled = false;
+  int32_t* perm = nullptr;
+  int32_t* inv = nullptr;
   // schedule: rows by degree, cost-balanced block ranges, chunked rows
   int32_t* order = nullptr;
   int64_t* cta_pos = nullptr;
@@ -68,6 +73,8 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init);
 cluster_status read_state(cluster_ctx* c);
 void fill_report(const cluster_ctx* c, cluster_report* rep);
 cluster_status finalize_loss(cluster_ctx* c);  // make the report's f the loss of the output iterate
+// U_out (n x k, the caller's numbering) from an internal n x KP iterate
+void unpad_output(const cluster_ctx* c, const float* X, float* U_out, cudaStream_t s);
 int grid_for(int64_t work, int threads = 256);
 
 // Non-owning batch over instances owned by the caller (batch.cu).

@@ -323,3 +323,30 @@ def test_sampled_rows_at_one_million_articles():
     rows = np.unique(np.concatenate([rng.integers(0, n, 3000), np.argsort(deg)[-50:]]))
     ref = oracle.fista_step_rows(S, X1, X2, beta, tau, rows)
     assert maxabs(X0[rows], ref) <= TOL_U
+
+
+def test_internal_degree_numbering_is_invisible_to_the_caller():
+    # relabel = 1 (default) numbers articles by degree inside the library; U0,
+    # U and the losses stay in the caller's numbering and agree with relabel = 0
+    spec = synth.GraphSpec("dcsbm", 20000, 16, 41, mean_deg=25.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, 16, 41, device="cuda")
+    runs = []
+    for relabel in (1, 0):
+        s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=30, relabel=relabel)
+        rep = s.step(30)
+        runs.append((s.get_U().cpu().numpy(), rep, s))
+    (Ua, ra, sa), (Ub, rb, sb) = runs
+    # the two numberings sum the Gram partials in different orders: float32 rounding only
+    assert maxabs(Ua, Ub) <= TOL_U
+    assert abs(ra["f"] - rb["f"]) <= TOL_F * abs(rb["f"])
+    S = to_scipy(rp, c, v, spec.n)
+    o = oracle.fista(S, U0.cpu().numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=30, stop="none")
+    assert maxabs(Ua, o.U) <= TOL_U
+    # a checkpoint records the numbering and is refused by a context with the other one
+    buf = sa.get_state()
+    with pytest.raises(pkg.ClusterError) as ei:
+        sb.set_state(buf)
+    assert ei.value.status == pkg.EINVAL
+    sa.close()
+    sb.close()
