@@ -36,7 +36,8 @@ METRIC = "PG iters/s, mixed vs FP32, at equal objective (n=70M,k=32); serving p9
 UNIT = "iter/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k32_n70M.json")
 SPMM_SRC = [os.path.join(ROOT, "paper_2506_04045_b300", "csrc", f)
-            for f in ("iter_common.cuh", "spmm_kernels.cuh", "state.h", "schedule.cuh", "init_kernels.cuh")]
+            for f in ("iter_common.cuh", "spmm_kernels.cuh", "state.h", "schedule.cuh", "init_kernels.cuh",
+                      "solver.cu")]
 
 
 def parse():
@@ -208,8 +209,9 @@ def update_bytes(n, k, mixed):
 
 
 def kernel_digest() -> str:
-    """Digest of the dominant (gather) kernel's sources and of the row schedule
-    it follows: the traffic figures stay valid while these files are unchanged."""
+    """Digest of the dominant (gather) kernel's sources, the row schedule it
+    follows and the solver that launches it (its L2 window): the traffic
+    figures stay valid while these files are unchanged."""
     h = hashlib.sha256()
     for path in SPMM_SRC:
         with open(path, "rb") as fh:

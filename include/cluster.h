@@ -125,7 +125,10 @@ typedef struct cluster_options {
                           outputs keep the caller's numbering, each row's sum
                           keeps its order, only the Gram partial order differs.
                           0 = keep the caller's numbering.                      */
-  int32_t _pad;
+  int32_t l2_window;   /* 1 = with relabel, keep the gathered rows of the
+                          highest-degree articles in a persisting L2 window
+                          (half the device's persisting maximum; default);
+                          0 = no window.  A cache hint: no value changes.       */
 } cluster_options;
 
 /* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */

@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("accel", ctypes.c_int32), ("borrow", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("graph_chunk", ctypes.c_int32), ("fused_pass", ctypes.c_int32), ("relabel", ctypes.c_int32),
-                ("_pad", ctypes.c_int32)]
+                ("l2_window", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

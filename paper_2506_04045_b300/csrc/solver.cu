@@ -113,6 +113,25 @@ struct KPOps {
     if (mixed) spmm_kernel<KP, true><<<grid, L::NT, 0, s>>>(a);
     else spmm_kernel<KP, false><<<grid, L::NT, 0, s>>>(a);
   }
+  // the same launch with a persisting L2 window over [base, base + bytes)
+  static void launch_spmm_window(const PassArgs& a, int grid, bool mixed, cudaStream_t s, void* base, size_t bytes) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(L::NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = base;
+    at[0].val.accessPolicyWindow.num_bytes = bytes;
+    at[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (mixed) cudaLaunchKernelEx(&cfg, spmm_kernel<KP, true>, a);
+    else cudaLaunchKernelEx(&cfg, spmm_kernel<KP, false>, a);
+  }
   static void launch_finalize(const PassArgs& a, cudaStream_t s) {
     const int64_t threads = a.n_heavy * L::T;
     int grid = (int)std::min<int64_t>((threads + 255) / 256, 4096);
@@ -184,6 +203,10 @@ static void kp_launch_spmm(int KP, const PassArgs& a, int grid, bool mixed, cuda
   FC_DISPATCH(KP, Ops::launch_spmm(a, grid, mixed, s));
 }
 static void kp_launch_finalize(int KP, const PassArgs& a, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_finalize(a, s)); }
+static void kp_launch_spmm_window(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s, void* base,
+                                  size_t bytes) {
+  FC_DISPATCH(KP, Ops::launch_spmm_window(a, grid, mixed, s, base, bytes));
+}
 static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
   FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, s));
 }
@@ -230,7 +253,9 @@ static cluster_status check_csr_args(const cluster_csr* S, int32_t k) {
 // ---------------------------------------------------------------------------
 void ctx_free(cluster_ctx* c) {
   if (!c) return;
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (cudaGraphExec_t g : c->graph_exec)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->l2_window_bytes) cudaCtxResetPersistingL2Cache();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
@@ -289,10 +314,16 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
 }
 
 // Enqueue one iteration (heavy chunks, fused pass, fold).
-static void enqueue_pass(const cluster_ctx* c, cudaStream_t s) {
+// One pass; `parity` is the pass counter's parity when it runs (it selects
+// the iterate buffer the gather reads and so the L2 window).
+static void enqueue_pass(const cluster_ctx* c, cudaStream_t s, int parity) {
   PassArgs a = make_pass_args(c, false);
   if (c->split) {
-    kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+    if (c->l2_window_bytes)
+      kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
+                            c->mixed ? (void*)c->XS[parity & 1] : (void*)c->X[parity & 1], c->l2_window_bytes);
+    else
+      kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
     if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
     kp_launch_update(c->KP, a, c->parts_upd, c->mixed, s);
   } else {
@@ -314,6 +345,7 @@ static void enqueue_eval(const cluster_ctx* c, int sel, int init, cudaStream_t s
 cluster_status read_state(cluster_ctx* c) {
   FC_CUDA(cudaMemcpyAsync(&c->host_st, c->st, sizeof(FistaState), cudaMemcpyDeviceToHost, c->stream));
   FC_CUDA(cudaStreamSynchronize(c->stream));
+  c->pass_guess = c->host_st.pass;
   return CLUSTER_OK;
 }
 
@@ -376,15 +408,18 @@ static cluster_status power_norm(cluster_ctx* c, double* out) {
 }
 
 static cluster_status capture_graph(cluster_ctx* c) {
-  cudaGraph_t g = nullptr;
-  FC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < c->graph_chunk; ++i) enqueue_pass(c, c->cap_stream);
-  FC_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
-  cudaError_t e = cudaGraphInstantiate(&c->graph_exec, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    set_error("graph instantiate: %s", cudaGetErrorString(e));
-    return CLUSTER_ECUDA;
+  const int variants = c->l2_window_bytes ? 2 : 1;
+  for (int p0 = 0; p0 < variants; ++p0) {
+    cudaGraph_t g = nullptr;
+    FC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < c->graph_chunk; ++i) enqueue_pass(c, c->cap_stream, p0 + i);
+    FC_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&c->graph_exec[p0], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_error("graph instantiate: %s", cudaGetErrorString(e));
+      return CLUSTER_ECUDA;
+    }
   }
   return CLUSTER_OK;
 }
@@ -608,6 +643,24 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   h.f_iter = 0;
   FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
   FC_CUDA(cudaStreamSynchronize(s));
+  c->pass_guess = 0;
+  // persisting L2 window over the gathered rows of the highest-degree
+  // articles (the first rows in the internal numbering): half of the
+  // device's persisting maximum, which measured best at n = 70M, k = 32
+  if (c->split && c->relabeled && opt.l2_window) {
+    int maxp = 0, maxw = 0;
+    FC_CUDA(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, c->dev));
+    FC_CUDA(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, c->dev));
+    const size_t rowb = (size_t)c->KP * (c->mixed ? 2 : 4);
+    size_t want = std::min<size_t>((size_t)maxp / 2, (size_t)maxw);
+    want = std::min<size_t>(want, rowb * (size_t)n);
+    if (want >= ((size_t)1 << 20)) {
+      size_t cur = 0;
+      FC_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+      if (cur < want) FC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+      c->l2_window_bytes = want;
+    }
+  }
   if (capture) FC_TRY(capture_graph(c));
   return CLUSTER_OK;
 }
@@ -715,6 +768,7 @@ extern "C" void cluster_options_default(cluster_options* opt) {
   opt->graph_chunk = 16;
   opt->fused_pass = 0;
   opt->relabel = 1;
+  opt->l2_window = 1;
 }
 
 extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
@@ -747,7 +801,13 @@ extern "C" cluster_status cluster_enqueue(cluster_ctx* c, int64_t iters) {
   FC_CUDA(cudaSetDevice(c->dev));
   set_limit_kernel<<<1, 1, 0, c->stream>>>(c->st, iters);
   const int64_t reps = (iters + c->graph_chunk - 1) / c->graph_chunk;
-  for (int64_t r = 0; r < reps; ++r) FC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+  for (int64_t r = 0; r < reps; ++r) {
+    // the graph whose window follows the buffers of the expected passes (a
+    // wrong guess, e.g. after an early stop, only costs cache hits)
+    const int par = c->graph_exec[1] ? (int)((c->pass_guess + r * c->graph_chunk) & 1) : 0;
+    FC_CUDA(cudaGraphLaunch(c->graph_exec[par], c->stream));
+  }
+  c->pass_guess += iters;
   FC_CUDA(cudaGetLastError());
   return CLUSTER_OK;
 }
@@ -770,7 +830,12 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
     cudaEvent_t* e = &ev[(size_t)(5 * i)];
     cudaEventRecord(e[0], s);
     if (c->split) {
-      kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+      const int par = (int)((c->pass_guess + i) & 1);
+      if (c->l2_window_bytes)
+        kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
+                              c->mixed ? (void*)c->XS[par] : (void*)c->X[par], c->l2_window_bytes);
+      else
+        kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
       cudaEventRecord(e[1], s);
       if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
       cudaEventRecord(e[2], s);
@@ -785,6 +850,7 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
     kp_launch_fold(c->KP, f, s);
     cudaEventRecord(e[4], s);
   }
+  c->pass_guess += iters;
   cudaError_t err = cudaStreamSynchronize(s);
   if (err == cudaSuccess) err = cudaGetLastError();
   double th = 0, tp = 0, tf = 0, tu = 0;
@@ -952,6 +1018,7 @@ extern "C" cluster_status cluster_set_state(cluster_ctx* c, const void* buf, siz
   }
   FC_CUDA(cudaStreamSynchronize(c->stream));
   c->host_st = fs;
+  c->pass_guess = fs.pass;
   return CLUSTER_OK;
 }
 

@@ -58,9 +58,12 @@ struct cluster_ctx {
   double* sc_part = nullptr;
   fc::FistaState* st = nullptr;
   fc::FistaState host_st{};
-  // graph of graph_chunk passes
+  // graphs of graph_chunk passes, one per parity of the first pass (the
+  // gather's L2 window follows the iterate buffer it reads)
   int graph_chunk = 16;
-  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int64_t pass_guess = 0;       // the device's pass counter as the host expects it
+  size_t l2_window_bytes = 0;   // persisting window over the first rows of the gathered copy (0 = none)
 };
 
 namespace fc {
