@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--cpu-sample-n", type=int, default=1_000_000)
     p.add_argument("--cpu-iters", type=int, default=2)
     p.add_argument("--fused", action="store_true", help="one fused kernel per iteration instead of the split form")
+    p.add_argument("--relabel", type=int, default=1, choices=[0, 1],
+                   help="solver option relabel (internal numbering by degree; 1 = library default)")
     return p.parse_args()
 
 
@@ -346,7 +348,8 @@ def run_native(args, ws, rank, local):
     for form in forms:
         mixed = form == "mixed"
         s = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0)
+                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
+                       relabel=args.relabel)
         s.step(W)
         barrier()
         torch.cuda.synchronize()
@@ -514,7 +517,7 @@ def run_batch(args, ws, rank, local):
         mixed = form == "mixed"
         t1 = time.perf_counter()
         b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
+                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel)
         init_s = time.perf_counter() - t1
         desc = b.autotune(trials=1)
         b.step(W)
@@ -593,7 +596,7 @@ def run_er2(args, ws, rank, local):
         for accel in (1, 0):
             name = ("fista_" if accel else "gpa_") + form
             s = pkg.Solver(rp, col, val, U0, step_rule=pkg.STEP_CONST, tau=tau, stop_rule=pkg.STOP_NONE,
-                           max_iter=10 ** 9, borrow=1, accel=accel,
+                           max_iter=10 ** 9, borrow=1, accel=accel, relabel=args.relabel,
                            precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
             acc = []
             for _ in range(30):
@@ -671,10 +674,11 @@ def run_serve(args, ws, rank, local):
         pool.append((rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), U0.cpu().numpy()))
         del rp, c, v, U0
     torch.cuda.empty_cache()
-    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, stop_rule=pkg.STOP_PG_REL,
+    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel,
+                     stop_rule=pkg.STOP_PG_REL,
                      tol=args.serve_tol, max_iter=args.serve_max_iter, borrow_host=True)
     rng = random.Random(4 + rank)
-    tickets, submit_t = [], {}
+    tickets, submit_t, which = [], {}, {}
     depth = []
     stop_sampling = threading.Event()
 
@@ -697,10 +701,11 @@ def run_serve(args, ws, rank, local):
             delay = t_next - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            req = pool[rng.randrange(len(pool))]
-            tk = srv.submit(*req)
+            pi = rng.randrange(len(pool))
+            tk = srv.submit(*pool[pi])
             tickets.append(tk)
             submit_t[tk] = time.perf_counter()
+            which[tk] = pi
         t_arrivals_end = time.perf_counter()
         results = {}
         deadline = t_arrivals_end + args.drain
@@ -714,7 +719,7 @@ def run_serve(args, ws, rank, local):
                     results[tk] = ("error", str(exc))
                     continue
                 if out is not None:
-                    results[tk] = ("ok", out[2], out[1])
+                    results[tk] = ("ok", out[2], out[1], which[tk])
             time.sleep(0.05)
         t_end = time.perf_counter()
         stop_sampling.set()
@@ -739,6 +744,8 @@ def run_serve(args, ws, rank, local):
             "mean_queue_s": float(np.mean([r[1]["queue_s"] for r in ok])) if ok else None,
             "mean_run_s": float(np.mean([r[1]["run_s"] for r in ok])) if ok else None,
             "iterations_of_completed": [int(r[2]["iters"]) for r in ok][:50],
+            "requests": [[specs[r[3]].n, specs[r[3]].k, round(r[1]["queue_s"], 4), round(r[1]["run_s"], 4),
+                          round(r[1]["total_s"], 4)] for r in ok][:200],
             "queue_depth": depth[::max(1, len(depth) // 40)], "server_stats": st, "clocks": cs.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -181,6 +181,16 @@ static cluster_status admit(cluster_server* sv, Request* r, cudaStream_t s) {
   cluster_status st = r->ctx ? init_impl(&S, r->k, d_U0, &o, s, r->ctx, false) : CLUSTER_ENOMEM;
   cudaStreamSynchronize(s);
   cudaFree(d_U0);
+  if (st == CLUSTER_OK && r->ctx->relabeled) {
+    // the context keeps its own renumbered copy of S: the uploaded one is no
+    // longer referenced (the footprint counts one copy)
+    cudaFree(r->d_rp);
+    cudaFree(r->d_col);
+    cudaFree(r->d_val);
+    r->d_rp = nullptr;
+    r->d_col = nullptr;
+    r->d_val = nullptr;
+  }
   // the device has its own copy now
   r->rp.clear();
   r->rp.shrink_to_fit();

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cub/cub.cuh>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -251,11 +252,36 @@ static cluster_status check_csr_args(const cluster_csr* S, int32_t k) {
 // ---------------------------------------------------------------------------
 // context helpers
 // ---------------------------------------------------------------------------
+// The persisting L2 set-aside is a limit of the process's CUDA context,
+// shared by all solvers: raised while at least one solver with a window
+// lives, restored (and persisting lines reset) when the last one goes.
+static std::mutex g_l2_mu;
+static int g_l2_users = 0;
+static size_t g_l2_saved = 0;
+
+static cluster_status l2_setaside_acquire(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_l2_mu);
+  size_t cur = 0;
+  FC_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  if (g_l2_users == 0) g_l2_saved = cur;
+  if (cur < bytes) FC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes));
+  ++g_l2_users;
+  return CLUSTER_OK;
+}
+
+static void l2_setaside_release() {
+  std::lock_guard<std::mutex> lk(g_l2_mu);
+  if (g_l2_users > 0 && --g_l2_users == 0) {
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_saved);
+  }
+}
+
 void ctx_free(cluster_ctx* c) {
   if (!c) return;
   for (cudaGraphExec_t g : c->graph_exec)
     if (g) cudaGraphExecDestroy(g);
-  if (c->l2_window_bytes) cudaCtxResetPersistingL2Cache();
+  if (c->l2_window_bytes) l2_setaside_release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
@@ -577,8 +603,14 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     if (pu > tiles) pu = tiles;
     c->parts_upd = (int)std::max<int64_t>(1, pu);
   }
-  // rows above H nonzeros (about 64 KB of gathered float32 data) are chunked
-  c->heavy_H = std::max<int64_t>(64, 16384 / c->KP);
+  // rows above H nonzeros are chunked: H is about 64 KB of gathered float32
+  // data, and at most an eighth of a resident gather warp's share of the
+  // nonzeros, so that in a small problem no unit (a team takes up to 4 rows
+  // of a unit in turn) sets the critical path of the launch
+  {
+    const int64_t warps = (int64_t)(c->split ? c->spmm_grid : c->heavy_grid) * 8;
+    c->heavy_H = std::max<int64_t>(64, std::min<int64_t>(16384 / c->KP, nnz / std::max<int64_t>(1, 8 * warps)));
+  }
   c->row_cost = 6;
   FC_TRY(build_schedule(c));
 
@@ -647,7 +679,9 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   // persisting L2 window over the gathered rows of the highest-degree
   // articles (the first rows in the internal numbering): half of the
   // device's persisting maximum, which measured best at n = 70M, k = 32
-  if (c->split && c->relabeled && opt.l2_window) {
+  // (solo solvers only: the batched kernels take no window, and a set-aside
+  // only shrinks the L2 they share)
+  if (capture && c->split && c->relabeled && opt.l2_window) {
     int maxp = 0, maxw = 0;
     FC_CUDA(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, c->dev));
     FC_CUDA(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, c->dev));
@@ -655,9 +689,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     size_t want = std::min<size_t>((size_t)maxp / 2, (size_t)maxw);
     want = std::min<size_t>(want, rowb * (size_t)n);
     if (want >= ((size_t)1 << 20)) {
-      size_t cur = 0;
-      FC_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
-      if (cur < want) FC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+      FC_TRY(l2_setaside_acquire(want));
       c->l2_window_bytes = want;
     }
   }
