@@ -159,9 +159,13 @@ CLUSTER_API const char* cluster_last_error(void);
 /* Create a solver for S (device CSR) with k clusters (1 <= k <= 128) from
  * the start point U0 (device, n x k; every row must be on the simplex to
  * within 1e-5).  Validates the inputs (EINVAL on failure), computes ||S||_F^2
- * and the step size, orders the rows by degree for load balance, and
- * evaluates the Gram matrix of U0.  The context keeps its own copy of U0.
- * Work is enqueued on `stream`; the call returns after it completes.
+ * and the step size, numbers the articles internally by degree (opt->relabel;
+ * the context then keeps its own renumbered copy of S even with borrow = 1),
+ * builds the gather schedule, and evaluates the Gram matrix of U0.  The
+ * context keeps its own copy of U0.  With opt->l2_window it raises the
+ * context's persisting L2 limit while it lives (restored when the last such
+ * solver is destroyed).  Work is enqueued on `stream`; the call returns after
+ * it completes.
  * Sect. 3, Algorithm 4 "initialize"; Sect. 5 "Hyperparameters". */
 CLUSTER_API cluster_status cluster_init(const cluster_csr* S, int32_t k, const float* U0,
                                         const cluster_options* opt, void* stream,

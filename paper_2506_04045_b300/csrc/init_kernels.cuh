@@ -1,5 +1,6 @@
-// Set-up kernels: input validation, ||S||_F^2, degree ordering, cost-balanced
-// block ranges, padding copies, and power iteration for ||S||_2.
+// Set-up kernels: input validation, ||S||_F^2, degree ordering and the internal
+// numbering, cost-balanced block ranges, padding copies, and power iteration
+// for ||S||_2.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

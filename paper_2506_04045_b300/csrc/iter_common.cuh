@@ -5,8 +5,8 @@
 //
 // Layout: a "team" of T lanes owns one row; lane t holds VEC consecutive
 // features of the row (KP padded features, rows of KP floats in HBM).  Teams
-// of one warp take rows of similar degree (rows are visited in degree order),
-// so the gather loop is warp-uniform.
+// of one warp take rows of similar degree (neighbouring positions of the
+// processing order have similar degrees), so the gather loop is warp-uniform.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

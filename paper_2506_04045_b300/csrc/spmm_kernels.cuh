@@ -10,9 +10,10 @@ namespace fc {
 // Z_{(pass+1)&1}, plus the partial products of chunked rows.  Pure gather, no
 // per-tile barrier: warps take work units from a global counter (units of
 // TPW chunks first, then units of TPW * kRowsPerUnit consecutive positions of
-// the degree order, so the teams of a warp have equal trip counts).  Each
-// row's result is computed by exactly one team in a fixed order, so the
-// dynamic schedule does not change any value.
+// the processing order, whose neighbouring positions hold rows of similar
+// degree, so the teams of a warp have about equal trip counts).  Each row's
+// result is computed by exactly one team in a fixed order, so the dynamic
+// schedule does not change any value.
 constexpr int kRowsPerUnit = 4;
 
 // Work units of one instance's gather: chunk units, then row units.
