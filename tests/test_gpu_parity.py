@@ -350,3 +350,9 @@ def test_internal_degree_numbering_is_invisible_to_the_caller():
     assert ei.value.status == pkg.EINVAL
     sa.close()
     sb.close()
+    # the L2 window is a cache hint and int32 row pointers are widened: neither changes a bit
+    for kw, rpk in (({"l2_window": 0}, rp), ({}, rp.to(torch.int32))):
+        s = pkg.Solver(rpk, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=30, **kw)
+        s.step(30)
+        assert torch.equal(s.get_U(), torch.from_numpy(Ua).cuda()), kw
+        s.close()
