@@ -130,7 +130,7 @@ cluster_status run_static(const cluster_csr* S, int32_t k, const float* U, cudaS
   fa.eval = 1;
   fa.eval_init = 0;
   fa.A = A;
-  fc::fold_kernel<KP><<<(KP * KP + 255) / 256, 256, 0, s>>>(fa);
+  fc::fold_kernel<KP><<<fc::fold_blocks<KP>(true), 256, 0, s>>>(fa);
   FC_CUDA(cudaGetLastError());
   FC_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
   FC_CUDA(cudaStreamSynchronize(s));

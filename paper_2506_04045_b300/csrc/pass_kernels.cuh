@@ -680,9 +680,16 @@ struct FoldArgs {
 // Xbar^{n-1}, applies the stop rule, advances t and the momentum factors, and
 // stores G(Y^{n+1}) minus its mean entry in float32 (the mean shift leaves the
 // projection unchanged because rows of Y sum to one: P(v + c 1) = P(v)).
+// First stage: each block sums the partials of FOLD_EPB entries, its 256
+// threads split into 256 / FOLD_EPB groups that take every group-th partial;
+// the group sums are then added in group order (a fixed tree: deterministic).
+template <int KP>
+__host__ __device__ constexpr int fold_epb() {
+  return KP <= 32 ? 32 : (KP == 64 ? 64 : 128);
+}
 template <int KP>
 __host__ __device__ constexpr int fold_blocks(bool eval) {
-  return ((eval ? 1 : 2) * KP * KP + 255) / 256;
+  return ((eval ? 1 : 2) * KP * KP + fold_epb<KP>() - 1) / fold_epb<KP>();
 }
 
 // Block `blk` of the `nblocks` blocks folding one instance (256 threads).
@@ -696,13 +703,26 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   const int64_t nnew = pass + 1;
   const int tid = threadIdx.x;
   const int nent = f.eval ? E2 : 2 * E2;
-  const int e = blk * 256 + tid;
-  if (e < nent) {
-    const int m = e / E2, r = (e % E2) / KP, c = e % KP;
-    const int src = m * E2 + ((r <= c) ? r * KP + c : c * KP + r);
+  {
+    constexpr int EPB = fold_epb<KP>(), GR = 256 / EPB;
+    __shared__ double gsum[256];
+    const int el = tid % EPB, g = tid / EPB;
+    const int e = blk * EPB + el;
     double s = 0.0;
-    for (int p = 0; p < f.parts; ++p) s += (double)f.gram_part[(size_t)p * 2 * E2 + src];
-    (m == 0 ? f.A : f.G)[r * KP + c] = s;
+    int src = 0;
+    if (e < nent) {
+      const int m = e / E2, r = (e % E2) / KP, c = e % KP;
+      src = m * E2 + ((r <= c) ? r * KP + c : c * KP + r);
+      for (int p = g; p < f.parts; p += GR) s += (double)f.gram_part[(size_t)p * 2 * E2 + src];
+    }
+    gsum[tid] = s;
+    __syncthreads();
+    if (g == 0 && e < nent) {
+      double t = gsum[el];
+      for (int q = 1; q < GR; ++q) t += gsum[q * EPB + el];
+      const int m = e / E2, r = (e % E2) / KP, c = e % KP;
+      (m == 0 ? f.A : f.G)[r * KP + c] = t;
+    }
   }
   __threadfence();
   __syncthreads();

@@ -145,7 +145,7 @@ struct KPOps {
   }
   static void launch_fold(const FoldArgs& f, cudaStream_t s) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
-    fold_kernel<KP><<<(nent + 255) / 256, 256, 0, s>>>(f);
+    fold_kernel<KP><<<(nent + fold_epb<KP>() - 1) / fold_epb<KP>(), 256, 0, s>>>(f);
   }
 };
 
