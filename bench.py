@@ -71,6 +71,9 @@ def parse():
     p.add_argument("--fused", action="store_true", help="one fused kernel per iteration instead of the split form")
     p.add_argument("--relabel", type=int, default=1, choices=[0, 1],
                    help="solver option relabel (internal numbering by degree; 1 = library default)")
+    p.add_argument("--update-engine", type=int, default=0, choices=[0, 1],
+                   help="solver option update_engine (0 = tcgen05 for 17 <= k <= 32, library default; "
+                        "1 = warp-level mma.sync); the two give the same bits")
     return p.parse_args()
 
 
@@ -349,7 +352,7 @@ def run_native(args, ws, rank, local):
         mixed = form == "mixed"
         s = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
                        precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
-                       relabel=args.relabel)
+                       relabel=args.relabel, update_engine=args.update_engine)
         s.step(W)
         barrier()
         torch.cuda.synchronize()
@@ -429,6 +432,7 @@ def run_native(args, ws, rank, local):
                    "l2": "inputs larger than L2 (S 16 GB, iterate 9 GB); no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "iteration_form": "fused" if args.fused else "split",
+                   "update_engine": "warp mma.sync" if args.update_engine else "tcgen05 (TMEM accumulators)",
                    "gen_seconds": round(gen_s, 1)},
         "forms": {f: {"it_s": res[f]["it_s"], "ms_per_step": res[f]["ms_total"] / K, "objective": res[f]["f"],
                       "pass_ms": res[f]["kt"]["pass_ms"], "heavy_ms": res[f]["kt"]["heavy_ms"],
@@ -467,7 +471,8 @@ def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
     for h, d in ((h_rp, d_rp), (h_col, d_col), (h_val, d_val), (h_U0, d_U0)):
         d.copy_(h, non_blocking=True)
     s = pkg.Solver(d_rp, d_col, d_val, d_U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                   precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0)
+                   precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
+                   relabel=args.relabel, update_engine=args.update_engine)
     losses = []
     for _ in range(K):
         losses.append(s.step(1)["f"])
@@ -517,7 +522,7 @@ def run_batch(args, ws, rank, local):
         mixed = form == "mixed"
         t1 = time.perf_counter()
         b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel)
+                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel, update_engine=args.update_engine)
         init_s = time.perf_counter() - t1
         desc = b.autotune(trials=1)
         b.step(W)
@@ -596,7 +601,7 @@ def run_er2(args, ws, rank, local):
         for accel in (1, 0):
             name = ("fista_" if accel else "gpa_") + form
             s = pkg.Solver(rp, col, val, U0, step_rule=pkg.STEP_CONST, tau=tau, stop_rule=pkg.STOP_NONE,
-                           max_iter=10 ** 9, borrow=1, accel=accel, relabel=args.relabel,
+                           max_iter=10 ** 9, borrow=1, accel=accel, relabel=args.relabel, update_engine=args.update_engine,
                            precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
             acc = []
             for _ in range(30):
@@ -674,7 +679,7 @@ def run_serve(args, ws, rank, local):
         pool.append((rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), U0.cpu().numpy()))
         del rp, c, v, U0
     torch.cuda.empty_cache()
-    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel,
+    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel, update_engine=args.update_engine,
                      stop_rule=pkg.STOP_PG_REL,
                      tol=args.serve_tol, max_iter=args.serve_max_iter, borrow_host=True)
     rng = random.Random(4 + rank)

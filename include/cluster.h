@@ -129,6 +129,12 @@ typedef struct cluster_options {
                           highest-degree articles in a persisting L2 window
                           (half the device's persisting maximum; default);
                           0 = no window.  A cache hint: no value changes.       */
+  int32_t update_engine; /* tensor cores of the row-local update for
+                          17 <= k <= 32: 0 = tcgen05.mma with accumulators in
+                          tensor memory (default); 1 = warp-level mma.sync.
+                          The two compute the same products in the same order:
+                          the same bits.  Other k always use mma.sync (16 < k
+                          <= 64) or float32 FMA.                                */
 } cluster_options;
 
 /* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */
@@ -269,6 +275,15 @@ CLUSTER_API cluster_status cluster_hessian_apply(const cluster_csr* S, int32_t k
 CLUSTER_API cluster_status cluster_state_size(cluster_ctx* ctx, size_t* bytes);
 CLUSTER_API cluster_status cluster_get_state(cluster_ctx* ctx, void* host_buf, size_t bytes);
 CLUSTER_API cluster_status cluster_set_state(cluster_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Test hook for the timeout path.  flags bit 0: the tcgen05 update (k in
+ * 17..32 with update_engine 0) still issues its y G products but withholds
+ * the commit that signals their completion, so its bounded waits give up
+ * after about one second; the run then ends with report status
+ * CLUSTER_ETIMEOUT, out_iter names the last complete iterate and the context
+ * stays usable (report, U, checkpoint).  flags 0 restores normal operation.
+ * Synchronises the context's stream.  EINVAL for a NULL context, ECUDA. */
+CLUSTER_API cluster_status cluster_test_hooks(cluster_ctx* ctx, int32_t flags);
 
 /* Release everything the context owns.  NULL is ignored. */
 CLUSTER_API void cluster_destroy(cluster_ctx* ctx);

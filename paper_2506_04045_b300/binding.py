@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("accel", ctypes.c_int32), ("borrow", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("graph_chunk", ctypes.c_int32), ("fused_pass", ctypes.c_int32), ("relabel", ctypes.c_int32),
-                ("l2_window", ctypes.c_int32)]
+                ("l2_window", ctypes.c_int32), ("update_engine", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -111,6 +111,7 @@ _SIGS = {
     "cluster_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cluster_destroy": (None, [_P]),
+    "cluster_test_hooks": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cluster_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(CSR), ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(_P), ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
     "cluster_batch_enqueue": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -275,6 +276,10 @@ class Solver:
     def set_state(self, buf: np.ndarray) -> None:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         check(self._lib.cluster_set_state(self._ctx, buf.ctypes.data, buf.nbytes))
+
+    def test_hooks(self, flags: int) -> None:
+        """cluster_test_hooks: bit 0 makes the tcgen05 update's waits give up."""
+        check(self._lib.cluster_test_hooks(self._ctx, int(flags)))
 
     def close(self) -> None:
         if self._ctx:

@@ -24,6 +24,7 @@ namespace {
 struct BatchClass {
   int KP = 0;
   bool mixed = false;
+  bool tc = true;            // update on tcgen05 (cluster_options.update_engine == 0)
   std::vector<int> members;  // instance indices
   // device copies of the per-instance tables
   PassArgs* d_args = nullptr;
@@ -47,22 +48,31 @@ struct BatchClass {
 template <int KP>
 struct BOps {
   using L = Lay<KP>;
+  using UpdFn = void (*)(BatchMeta);
+  static bool use_tc(bool tc) { return tc && TcUpd<KP>::ON; }
+  static UpdFn upd_fn(bool mixed, bool tc) {
+    if constexpr (TcUpd<KP>::ON) {
+      if (tc) return mixed ? batch_update_kernel<KP, true, true> : batch_update_kernel<KP, false, true>;
+    }
+    return mixed ? batch_update_kernel<KP, true, false> : batch_update_kernel<KP, false, false>;
+  }
+  static size_t upd_smem(bool tc) { return use_tc(tc) ? TcUpd<KP>::smem() : pass_smem_bytes<KP>(false); }
   static cudaError_t setup() {
-    const int smem = (int)pass_smem_bytes<KP>(false);
-    cudaError_t e = cudaFuncSetAttribute(batch_update_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_update_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    for (int v = 0; v < (TcUpd<KP>::ON ? 4 : 2); ++v) {
+      const bool mixed = v & 1, tc = v >> 1;
+      cudaError_t e = cudaFuncSetAttribute(upd_fn(mixed, tc), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)upd_smem(tc));
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   static void grids(BatchClass& bc, int sms) {
     int o1 = 0, o2 = 0;
-    const size_t smem = pass_smem_bytes<KP>(false);
-    if (bc.mixed) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, true>, L::NT, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_update_kernel<KP, true>, L::NT, smem);
-    } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, false>, L::NT, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_update_kernel<KP, false>, L::NT, smem);
-    }
+    const size_t smem = upd_smem(bc.tc);
+    if (bc.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, true>, L::NT, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_spmm_kernel<KP, false>, L::NT, 0);
+    if (use_tc(bc.tc)) o2 = tc_blocks_per_sm((const void*)upd_fn(bc.mixed, true), L::NT, smem, TcUpd<KP>::TMEM_COLS);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, upd_fn(bc.mixed, false), L::NT, smem);
     bc.occ_spmm = std::max(1, o1);
     bc.occ_upd = std::max(1, o2);
     bc.spmm_grid = sms * std::max(1, o1);
@@ -74,12 +84,10 @@ struct BOps {
   }
   static void iteration(const BatchClass& bc, cudaStream_t s) {
     cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
-    const size_t smem = pass_smem_bytes<KP>(false);
     if (bc.mixed) batch_spmm_kernel<KP, true><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
     else batch_spmm_kernel<KP, false><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
     if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
-    if (bc.mixed) batch_update_kernel<KP, true><<<bc.upd_grid, L::NT, smem, s>>>(bc.meta);
-    else batch_update_kernel<KP, false><<<bc.upd_grid, L::NT, smem, s>>>(bc.meta);
+    upd_fn(bc.mixed, bc.tc)<<<bc.upd_grid, L::NT, upd_smem(bc.tc), s>>>(bc.meta);
     batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
   }
   static int64_t units(const cluster_ctx* c) {
@@ -89,15 +97,13 @@ struct BOps {
   // one iteration with events around the two persistent kernels
   static void timed_iteration(const BatchClass& bc, int spmm_grid, int upd_grid, cudaEvent_t* ev, cudaStream_t s) {
     cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
-    const size_t smem = pass_smem_bytes<KP>(false);
     cudaEventRecord(ev[0], s);
     if (bc.mixed) batch_spmm_kernel<KP, true><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
     else batch_spmm_kernel<KP, false><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
     cudaEventRecord(ev[1], s);
     if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
     cudaEventRecord(ev[2], s);
-    if (bc.mixed) batch_update_kernel<KP, true><<<upd_grid, L::NT, smem, s>>>(bc.meta);
-    else batch_update_kernel<KP, false><<<upd_grid, L::NT, smem, s>>>(bc.meta);
+    upd_fn(bc.mixed, bc.tc)<<<upd_grid, L::NT, upd_smem(bc.tc), s>>>(bc.meta);
     cudaEventRecord(ev[3], s);
     batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
   }
@@ -275,6 +281,7 @@ static cluster_status batch_assemble(cluster_batch* b) {
       BatchClass bc;
       bc.KP = c->KP;
       bc.mixed = c->mixed;
+      bc.tc = c->tc_update;
       cls[key] = (int)b->classes.size();
       b->classes.push_back(bc);
       it = cls.find(key);

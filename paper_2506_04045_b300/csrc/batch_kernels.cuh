@@ -6,6 +6,7 @@
 // batched instance computes bit for bit what it computes alone.
 #pragma once
 #include "pass_kernels.cuh"
+#include "tc_update.cuh"
 
 namespace fc {
 
@@ -71,10 +72,39 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(BatchMeta b) {
   }
 }
 
-template <int KP, bool MIXED>
+// TC: the tcgen05 update (KP = 32), else the warp-level one
+template <int KP, bool MIXED, bool TC>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) batch_update_kernel(BatchMeta b) {
-  extern __shared__ __align__(16) float smem[];
   __shared__ int item_s;
+  if constexpr (TC && TcUpd<KP>::ON) {
+    // the tcgen05 update of the solo solver, TMEM and barriers held across items
+    extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tslot;
+    __shared__ int tmo_flag[2];
+    TcBlock tb;
+    tc_begin<KP>(tb, tc_smem_raw, bars, &tslot, tmo_flag);
+    for (;;) {
+      if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
+      __syncthreads();
+      const int item = item_s;
+      __syncthreads();
+      if (item >= b.n_items) break;
+      const int j = b.item_inst[item];
+      const int slot = b.item_slot[item];
+      const PassArgs& a = b.args[j];
+      if (instance_idle(a.st)) continue;
+      const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+      const int parts = b.parts_upd[j];
+      const int64_t p0 = a.n * (int64_t)slot / parts;
+      const int64_t p1 = a.n * (int64_t)(slot + 1) / parts;
+      tc_update_range<KP, MIXED>(a, pass, p0, p1, slot, tb);
+      __syncthreads();
+    }
+    tc_end<KP>(tb);
+    return;
+  }
+  extern __shared__ __align__(16) float smem[];
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
     __syncthreads();

@@ -59,7 +59,7 @@ struct PassArgs {
   unsigned long long* work;  // split pass: work counter of spmm_kernel (reset by the fold)
   const float* Gy;           // KP x KP float32, G(Y) minus its mean entry
   float* gram_part;          // [gridDim.x][2][KP][KP]
-  double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite
+  double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite, waits given up
   FistaState* st;
   int64_t n;
   int32_t k;

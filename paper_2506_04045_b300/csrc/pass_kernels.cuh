@@ -748,13 +748,31 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   }
   const double gram2_new = red[0];
   __syncthreads();
-  if (tid == 0) {
-    double tr = 0, pg = 0, bad = 0;
-    for (int c = 0; c < f.parts; ++c) {
-      tr += __ldcg(f.sc_part + c * 4 + 0);
-      pg += __ldcg(f.sc_part + c * 4 + 1);
-      bad += __ldcg(f.sc_part + c * 4 + 2);
+  // block sums of the scalar partials: thread t takes partials t, t + 256, ...
+  // in order, then a fixed tree (deterministic)
+  __shared__ double sred[4][256];
+  {
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    for (int c = tid; c < f.parts; c += 256) {
+      v0 += __ldcg(f.sc_part + c * 4 + 0);
+      v1 += __ldcg(f.sc_part + c * 4 + 1);
+      v2 += __ldcg(f.sc_part + c * 4 + 2);
+      v3 += __ldcg(f.sc_part + c * 4 + 3);
     }
+    sred[0][tid] = v0;
+    sred[1][tid] = v1;
+    sred[2][tid] = v2;
+    sred[3][tid] = v3;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sred[q][tid] += sred[q][tid + o];
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    const double tr = sred[0][0], pg = sred[1][0], bad = sred[2][0], tmo = sred[3][0];
     if (f.eval) {
       st->eval_trace = tr;
       st->eval_gram2 = gram2_new;
@@ -772,7 +790,13 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
       if (nnew == 1) st->pg_first = r;
       int done = 0, status = 0;
       int64_t out = nnew;
-      if (bad > 0.0 || !isfinite(loss)) {
+      if (tmo > 0.0) {
+        // a bounded wait of the update gave up: Xbar^{pass} is the last
+        // complete iterate
+        done = 1;
+        status = 6;
+        out = pass;
+      } else if (bad > 0.0 || !isfinite(loss)) {
         done = 1;
         status = 4;
         out = pass;

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cub/cub.cuh>
 #include <mutex>
@@ -16,6 +17,7 @@
 
 #include "init_kernels.cuh"
 #include "pass_kernels.cuh"
+#include "tc_update.cuh"
 #include "hessian_kernels.cuh"
 #include "solver_impl.h"
 #include "util.h"
@@ -97,14 +99,29 @@ struct KPOps {
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_kernel<KP, false>, L::NT, 0);
     return occ < 1 ? 1 : occ;
   }
-  static int occ_update(bool mixed) {
+  // k <= 32: the tcgen05 update (tc_update.cuh) unless tc is false; otherwise
+  // the warp-level one
+  static int occ_update(bool mixed, bool tc) {
     int occ = 0;
+    if constexpr (TcUpd<KP>::ON) {
+      if (tc) {
+        const void* fn = mixed ? (const void*)update_tc_kernel<KP, true> : (const void*)update_tc_kernel<KP, false>;
+        return tc_blocks_per_sm(fn, L::NT, TcUpd<KP>::smem(), TcUpd<KP>::TMEM_COLS);
+      }
+    }
     const size_t smem = pass_smem_bytes<KP>(false);
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, true>, L::NT, smem);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, false>, L::NT, smem);
     return occ < 1 ? 1 : occ;
   }
   static cudaError_t setup_update_attr() {
+    if constexpr (TcUpd<KP>::ON) {
+      const int smem = (int)TcUpd<KP>::smem();
+      cudaError_t e = cudaFuncSetAttribute(update_tc_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(update_tc_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
     const int smem = (int)pass_smem_bytes<KP>(false);
     cudaError_t e = cudaFuncSetAttribute(update_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -138,7 +155,15 @@ struct KPOps {
     int grid = (int)std::min<int64_t>((threads + 255) / 256, 4096);
     heavy_finalize_kernel<KP><<<grid < 1 ? 1 : grid, 256, 0, s>>>(a);
   }
-  static void launch_update(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  static void launch_update(const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s) {
+    if constexpr (TcUpd<KP>::ON) {
+      if (tc) {
+        const size_t smem = TcUpd<KP>::smem();
+        if (mixed) update_tc_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
+        else update_tc_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
+        return;
+      }
+    }
     const size_t smem = pass_smem_bytes<KP>(false);
     if (mixed) update_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
     else update_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
@@ -190,9 +215,9 @@ static int kp_occ_spmm(int KP, bool mixed) {
   FC_DISPATCH(KP, o = Ops::occ_spmm(mixed));
   return o;
 }
-static int kp_occ_update(int KP, bool mixed) {
+static int kp_occ_update(int KP, bool mixed, bool tc) {
   int o = 1;
-  FC_DISPATCH(KP, o = Ops::occ_update(mixed));
+  FC_DISPATCH(KP, o = Ops::occ_update(mixed, tc));
   return o;
 }
 static cudaError_t kp_setup_update_attr(int KP) {
@@ -208,8 +233,8 @@ static void kp_launch_spmm_window(int KP, const PassArgs& a, int grid, bool mixe
                                   size_t bytes) {
   FC_DISPATCH(KP, Ops::launch_spmm_window(a, grid, mixed, s, base, bytes));
 }
-static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, s));
+static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, tc, s));
 }
 
 __global__ void set_limit_kernel(FistaState* st, int64_t iters) { st->limit = st->pass + iters; }
@@ -351,7 +376,7 @@ static void enqueue_pass(const cluster_ctx* c, cudaStream_t s, int parity) {
     else
       kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
     if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
-    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, s);
+    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
   } else {
     if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
     kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
@@ -596,10 +621,11 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->parts = (int)parts;
   c->heavy_grid = sms * occ;
   c->split = opt.fused_pass == 0;
+  c->tc_update = opt.update_engine == 0;
   if (c->split) {
     FC_CUDA(kp_setup_update_attr(c->KP));
     c->spmm_grid = sms * kp_occ_spmm(c->KP, c->mixed);
-    int64_t pu = (int64_t)sms * kp_occ_update(c->KP, c->mixed);
+    int64_t pu = (int64_t)sms * kp_occ_update(c->KP, c->mixed, c->tc_update);
     if (pu > tiles) pu = tiles;
     c->parts_upd = (int)std::max<int64_t>(1, pu);
   }
@@ -801,6 +827,7 @@ extern "C" void cluster_options_default(cluster_options* opt) {
   opt->fused_pass = 0;
   opt->relabel = 1;
   opt->l2_window = 1;
+  opt->update_engine = 0;
 }
 
 extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
@@ -871,7 +898,7 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
       cudaEventRecord(e[1], s);
       if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
       cudaEventRecord(e[2], s);
-      kp_launch_update(c->KP, a, c->parts_upd, c->mixed, s);
+      kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
     } else {
       if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
       cudaEventRecord(e[1], s);
@@ -935,6 +962,16 @@ extern "C" cluster_status cluster_get_report(cluster_ctx* c, cluster_report* rep
   if (!c) FC_EINVAL("ctx is NULL");
   FC_TRY(read_state(c));
   fill_report(c, rep);
+  return CLUSTER_OK;
+}
+
+extern "C" cluster_status cluster_test_hooks(cluster_ctx* c, int32_t flags) {
+  clear_error();
+  if (!c) FC_EINVAL("ctx is NULL");
+  FC_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(c->st) + offsetof(FistaState, hooks), &flags, sizeof(flags),
+                          cudaMemcpyHostToDevice, c->stream));
+  FC_CUDA(cudaStreamSynchronize(c->stream));
+  c->host_st.hooks = flags;
   return CLUSTER_OK;
 }
 

@@ -51,6 +51,7 @@ struct cluster_ctx {
   unsigned long long* work = nullptr;   // split iteration: gather kernel work counter
   bool split = true;
   int parts_upd = 1;                    // blocks (and partial slots) of the update kernel
+  bool tc_update = true;                // update on tcgen05 where the kernel exists (k <= 32)
   int spmm_grid = 1;
   double* A[2] = {nullptr, nullptr};  // float64 fold scratch: Gram of Xbar^n, Gram of Y^{n+1}
   float* Gy = nullptr;                 // float32 G(Y) (minus its mean) read by the next pass

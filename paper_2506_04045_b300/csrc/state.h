@@ -34,13 +34,13 @@ struct FistaState {
   int64_t f_iter;     // -1 until a loss is known
   int64_t out_iter;   // iterate cluster_get_U returns
   int32_t done;
-  int32_t status;     // 0 ok, 4 nonfinite, 5 max_iter
+  int32_t status;     // 0 ok, 4 nonfinite, 5 max_iter, 6 a bounded wait gave up
   int32_t stop_rule;
   int32_t accel;
   int32_t k;
   uint32_t ticket;    // block counter of the fold kernel (reset by its last block)
   int32_t eval_mode;
-  int32_t pad_;
+  int32_t hooks;      // test hooks (cluster_test_hooks); 0 in normal operation
   double eval_f;      // result of the last objective-only pass
   double eval_trace;
   double eval_gram2;

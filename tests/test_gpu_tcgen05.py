@@ -1,0 +1,95 @@
+"""The row-local update on the fifth-generation tensor cores (tcgen05.mma,
+accumulators in tensor memory; k in 17..32) against the warp-level mma.sync
+update: both compute the same 3xTF32 products in the same order, so every bit
+of the iterates, losses and norms agrees.  Also the bounded-wait path: a wait
+that gives up ends the run with CLUSTER_ETIMEOUT and leaves the context usable."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_helpers import maxabs, to_scipy
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2506_04045_b300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+
+
+def _run(rp, c, v, U0, iters, **kw):
+    s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=iters, **kw)
+    rep = s.step(iters)
+    U = s.get_U()
+    s.close()
+    return U, rep
+
+
+# n = 30011: 938 full tiles of 32 rows and a ragged one; k spans the kernel's range
+@pytest.mark.parametrize("k", [17, 24, 32])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tcgen05_update_equals_warp_update_bitwise(k, precision):
+    spec = synth.GraphSpec("dcsbm", 30011, k, 70 + k, mean_deg=25.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, k, 70 + k, device="cuda")
+    Ut, rt = _run(rp, c, v, U0, 25, precision=precision, update_engine=0)
+    Uw, rw = _run(rp, c, v, U0, 25, precision=precision, update_engine=1)
+    assert rt["iters"] == rw["iters"] == 25
+    assert torch.equal(Ut, Uw)
+    assert rt["f"] == rw["f"] and rt["pg_norm"] == rw["pg_norm"] and rt["trace_SU"] == rw["trace_SU"]
+    if precision == 0 and k == 32:
+        S = to_scipy(rp, c, v, spec.n)
+        o = oracle.fista(S, U0.cpu().numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=25,
+                         stop="none")
+        assert maxabs(Ut.cpu().numpy(), o.U) <= 1e-5
+
+
+def test_tcgen05_update_in_a_batch_equals_solo():
+    specs = [synth.GraphSpec("dcsbm", 9001, 32, 81, mean_deg=20.0),
+             synth.GraphSpec("dcsbm", 4000, 20, 82, mean_deg=30.0),
+             synth.GraphSpec("dcsbm", 700, 8, 83, mean_deg=12.0)]
+    inst = []
+    for sp in specs:
+        rp, c, v = synth.make_graph(sp)
+        U0 = synth.dirichlet_u0(sp.n, sp.k, sp.seed)
+        inst.append(tuple(t.cuda().contiguous() for t in (rp, c, v, U0)))
+    for eng in (0, 1):
+        b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=20, update_engine=eng)
+        b.step(20)
+        for i, (rp, c, v, U0) in enumerate(inst):
+            U, _ = _run(rp, c, v, U0, 20, update_engine=1 - eng)   # the other engine, alone
+            assert torch.equal(b.get_U(i), U), (eng, i)
+        b.close()
+
+
+def test_wait_that_gives_up_is_a_status_and_the_context_survives():
+    spec = synth.GraphSpec("dcsbm", 5000, 32, 91, mean_deg=20.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, 32, 91, device="cuda")
+    s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50)
+    s.step(3)
+    U3 = s.get_U().clone()
+    s.test_hooks(1)
+    t0 = time.time()
+    rep = s.step(5)
+    dt = time.time() - t0
+    assert rep["status"] == pkg.ETIMEOUT and rep["done"] == 1 and rep["out_iter"] == 3
+    assert dt < 60
+    assert torch.equal(s.get_U(), U3)          # the last complete iterate
+    assert s.report()["status"] == pkg.ETIMEOUT
+    assert s.state_size() > 0 and s.get_state().size > 0
+    s.test_hooks(0)
+    s.close()
+    # the device is still fine for the next context: the same three iterations, the same bits
+    s2 = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50)
+    s2.step(3)
+    assert torch.equal(s2.get_U(), U3)
+    s2.close()
