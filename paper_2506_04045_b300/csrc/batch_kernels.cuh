@@ -72,55 +72,57 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(BatchMeta b) {
   }
 }
 
-// TC: the tcgen05 update (KP = 32), else the warp-level one
+// Update items in a persistent loop: item -> (instance, partial slot), the
+// rows [n slot / parts, n (slot + 1) / parts) the instance's solo block of that
+// slot takes.
+__device__ __forceinline__ bool next_update_item(const BatchMeta& b, int& item_s, const PassArgs*& a, int& slot,
+                                                 int64_t& pass, int64_t& p0, int64_t& p1, bool& idle) {
+  if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
+  __syncthreads();
+  const int item = item_s;
+  __syncthreads();
+  if (item >= b.n_items) return false;
+  const int j = b.item_inst[item];
+  slot = b.item_slot[item];
+  a = &b.args[j];
+  idle = instance_idle(a->st);
+  if (idle) return true;
+  pass = ((const volatile FistaState*)a->st)->pass;
+  const int parts = b.parts_upd[j];
+  p0 = a->n * (int64_t)slot / parts;
+  p1 = a->n * (int64_t)(slot + 1) / parts;
+  return true;
+}
+
+// TC: the tcgen05 update (KP = 32; TMEM and barriers held across items), else
+// the warp-level one.
 template <int KP, bool MIXED, bool TC>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) batch_update_kernel(BatchMeta b) {
   __shared__ int item_s;
+  const PassArgs* a = nullptr;
+  int slot = 0;
+  int64_t pass = 0, p0 = 0, p1 = 0;
+  bool idle = false;
   if constexpr (TC && TcUpd<KP>::ON) {
-    // the tcgen05 update of the solo solver, TMEM and barriers held across items
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tslot;
     __shared__ int tmo_flag[2];
     TcBlock tb;
     tc_begin<KP>(tb, tc_smem_raw, bars, &tslot, tmo_flag);
-    for (;;) {
-      if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
-      __syncthreads();
-      const int item = item_s;
-      __syncthreads();
-      if (item >= b.n_items) break;
-      const int j = b.item_inst[item];
-      const int slot = b.item_slot[item];
-      const PassArgs& a = b.args[j];
-      if (instance_idle(a.st)) continue;
-      const int64_t pass = ((const volatile FistaState*)a.st)->pass;
-      const int parts = b.parts_upd[j];
-      const int64_t p0 = a.n * (int64_t)slot / parts;
-      const int64_t p1 = a.n * (int64_t)(slot + 1) / parts;
-      tc_update_range<KP, MIXED>(a, pass, p0, p1, slot, tb);
+    while (next_update_item(b, item_s, a, slot, pass, p0, p1, idle)) {
+      if (idle) continue;
+      tc_update_range<KP, MIXED>(*a, pass, p0, p1, slot, tb);
       __syncthreads();
     }
     tc_end<KP>(tb);
-    return;
-  }
-  extern __shared__ __align__(16) float smem[];
-  for (;;) {
-    if (threadIdx.x == 0) item_s = (int)atomicAdd(&b.work[1], 1ull);
-    __syncthreads();
-    const int item = item_s;
-    __syncthreads();
-    if (item >= b.n_items) break;
-    const int j = b.item_inst[item];
-    const int slot = b.item_slot[item];
-    const PassArgs& a = b.args[j];
-    if (instance_idle(a.st)) continue;
-    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
-    const int parts = b.parts_upd[j];
-    const int64_t p0 = a.n * (int64_t)slot / parts;
-    const int64_t p1 = a.n * (int64_t)(slot + 1) / parts;
-    pass_range<KP, MIXED, false, true>(a, pass, p0, p1, slot, smem);
-    __syncthreads();
+  } else {
+    extern __shared__ __align__(16) float smem[];
+    while (next_update_item(b, item_s, a, slot, pass, p0, p1, idle)) {
+      if (idle) continue;
+      pass_range<KP, MIXED, false, true>(*a, pass, p0, p1, slot, smem);
+      __syncthreads();
+    }
   }
 }
 

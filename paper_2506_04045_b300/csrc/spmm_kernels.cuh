@@ -68,8 +68,17 @@ __device__ __forceinline__ void spmm_unit(const PassArgs& a, int64_t pass, int64
   }
 }
 
+// Resident blocks per SM the gather's register budget is sized for: the
+// float32 k <= 32 gather (128-byte rows) ran 1.8% faster with 5 blocks (48
+// registers) than with 4 (58); the bfloat16 one (64-byte rows) 7% slower, and
+// 6 blocks were slower for both.  0: no bound (the compiler's choice).
 template <int KP, bool MIXED>
-__global__ void __launch_bounds__(Lay<KP>::NT) spmm_kernel(PassArgs a) {
+__host__ __device__ constexpr int spmm_min_blocks() {
+  return (KP == 32 && !MIXED) ? 5 : 0;
+}
+
+template <int KP, bool MIXED>
+__global__ void __launch_bounds__(Lay<KP>::NT, spmm_min_blocks<KP, MIXED>()) spmm_kernel(PassArgs a) {
   volatile FistaState* vs = a.st;
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
