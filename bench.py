@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--fused", action="store_true", help="one fused kernel per iteration instead of the split form")
     p.add_argument("--relabel", type=int, default=1, choices=[0, 1],
                    help="solver option relabel (internal numbering by degree; 1 = library default)")
+    p.add_argument("--overlap", type=int, default=0, choices=[0, 1],
+                   help="solver option overlap (update of row chunks beside the gather; 0 = library default)")
     p.add_argument("--update-engine", type=int, default=0, choices=[0, 1],
                    help="solver option update_engine (0 = tcgen05 for 17 <= k <= 32, library default; "
                         "1 = warp-level mma.sync); the two give the same bits")
@@ -352,7 +354,7 @@ def run_native(args, ws, rank, local):
         mixed = form == "mixed"
         s = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
                        precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
-                       relabel=args.relabel, update_engine=args.update_engine)
+                       relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
         s.step(W)
         barrier()
         torch.cuda.synchronize()
@@ -370,7 +372,7 @@ def run_native(args, ws, rank, local):
         f = pkg.objective(rp, col, val, U)
         rep = s.report()
         res[form] = {"ms_total": ms, "it_s": K / (ms / 1000.0), "kt": kt, "f": f, "iters": rep["iters"],
-                     "launches": 1 + K * (3 if kt["heavy_rows"] > 0 else 2) + (0 if args.fused else K)}
+                     "launches": kt["kernels"]}
         sampler_summary[form] = cs.summary()
         s.close()
         del s, U
@@ -433,6 +435,7 @@ def run_native(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "iteration_form": "fused" if args.fused else "split",
                    "update_engine": "warp mma.sync" if args.update_engine else "tcgen05 (TMEM accumulators)",
+                   "overlap": "update of 8 row chunks beside the gather" if args.overlap else "gather, then update",
                    "gen_seconds": round(gen_s, 1)},
         "forms": {f: {"it_s": res[f]["it_s"], "ms_per_step": res[f]["ms_total"] / K, "objective": res[f]["f"],
                       "pass_ms": res[f]["kt"]["pass_ms"], "heavy_ms": res[f]["kt"]["heavy_ms"],
@@ -472,7 +475,7 @@ def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
         d.copy_(h, non_blocking=True)
     s = pkg.Solver(d_rp, d_col, d_val, d_U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
                    precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
-                   relabel=args.relabel, update_engine=args.update_engine)
+                   relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
     losses = []
     for _ in range(K):
         losses.append(s.step(1)["f"])
@@ -522,7 +525,7 @@ def run_batch(args, ws, rank, local):
         mixed = form == "mixed"
         t1 = time.perf_counter()
         b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel, update_engine=args.update_engine)
+                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
         init_s = time.perf_counter() - t1
         desc = b.autotune(trials=1)
         b.step(W)
@@ -601,7 +604,7 @@ def run_er2(args, ws, rank, local):
         for accel in (1, 0):
             name = ("fista_" if accel else "gpa_") + form
             s = pkg.Solver(rp, col, val, U0, step_rule=pkg.STEP_CONST, tau=tau, stop_rule=pkg.STOP_NONE,
-                           max_iter=10 ** 9, borrow=1, accel=accel, relabel=args.relabel, update_engine=args.update_engine,
+                           max_iter=10 ** 9, borrow=1, accel=accel, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap,
                            precision=pkg.MIXED_BF16 if mixed else pkg.FP32)
             acc = []
             for _ in range(30):
@@ -679,7 +682,7 @@ def run_serve(args, ws, rank, local):
         pool.append((rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), U0.cpu().numpy()))
         del rp, c, v, U0
     torch.cuda.empty_cache()
-    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel, update_engine=args.update_engine,
+    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap,
                      stop_rule=pkg.STOP_PG_REL,
                      tol=args.serve_tol, max_iter=args.serve_max_iter, borrow_host=True)
     rng = random.Random(4 + rank)

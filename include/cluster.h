@@ -135,6 +135,14 @@ typedef struct cluster_options {
                           The two compute the same products in the same order:
                           the same bits.  Other k always use mma.sync (16 < k
                           <= 64) or float32 FMA.                                */
+  int32_t overlap;     /* 1 = with the internal numbering and n >= 2^20, run the
+                          update of each of 8 row chunks on a second stream as
+                          soon as the gather has produced that chunk's rows,
+                          beside the gather of the following chunks; 0 = gather,
+                          then update (default: the gather slows more beside the
+                          update than the overlap saves).  Such problems use 4
+                          update blocks per resident block either way, so the
+                          two schedules give the same bits.                     */
 } cluster_options;
 
 /* Progress of a solve.  Iteration n means the paper's Xbar^n (Xbar^0 = U0). */
@@ -190,7 +198,10 @@ CLUSTER_API cluster_status cluster_enqueue(cluster_ctx* ctx, int64_t iters);
 
 /* Per-kernel timing of the fused iteration, averaged over the launches of
  * one cluster_enqueue_profiled call (milliseconds, CUDA events on the
- * context's stream).  pass = the fused pass kernel, heavy = the kernel that
+ * context's stream).  With the overlapped pass (cluster_options.overlap),
+ * pass_ms runs from the start to the end of the last gather (hub-row sums
+ * included, heavy_ms = 0) and update_ms is the part of the updates after it.
+ * pass = the fused pass kernel, heavy = the kernel that
  * computes the partial products of chunked high-degree rows (0 if none),
  * fold = the float64 fold.  heavy_nnz is the number of nonzeros the heavy
  * kernel streams per iteration (the pass kernel streams nnz - heavy_nnz). */
@@ -203,6 +214,7 @@ typedef struct cluster_kernel_times {
   int64_t launches;    /* iterations timed                                     */
   int64_t heavy_nnz;
   int64_t heavy_rows;
+  int64_t kernels;     /* kernel launches of the library in the call           */
 } cluster_kernel_times;
 
 /* Run `iters` iterations launched one kernel at a time (no graph) with CUDA

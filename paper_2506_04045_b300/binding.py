@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("accel", ctypes.c_int32), ("borrow", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("graph_chunk", ctypes.c_int32), ("fused_pass", ctypes.c_int32), ("relabel", ctypes.c_int32),
-                ("l2_window", ctypes.c_int32), ("update_engine", ctypes.c_int32)]
+                ("l2_window", ctypes.c_int32), ("update_engine", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -59,7 +59,7 @@ class Report(ctypes.Structure):
 class KernelTimes(ctypes.Structure):
     _fields_ = [("pass_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double), ("fold_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("heavy_nnz", ctypes.c_int64),
-                ("heavy_rows", ctypes.c_int64)]
+                ("heavy_rows", ctypes.c_int64), ("kernels", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -310,4 +310,11 @@ static __global__ void fill_start_kernel(double* __restrict__ x, int64_t n) {
   }
 }
 
+// flag = 1 if order[p] != p for some p (the gather order is not the identity)
+static __global__ void order_identity_kernel(const int32_t* order, int64_t n, int* flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    if (order[p] != (int32_t)p) *flag = 1;
+}
+
 }  // namespace fc

@@ -57,6 +57,10 @@ struct PassArgs {
   float* Z0;                 // split pass: S Xbar^j in Z_{(j+1)&1}, n x KP float32
   float* Z1;
   unsigned long long* work;  // split pass: work counter of spmm_kernel (reset by the fold)
+  int64_t unit_lo;           // split pass: gather units [unit_lo, unit_hi) (unit_hi < 0: all)
+  int64_t unit_hi;
+  int32_t upd_block0;        // split pass: first block of this update launch among
+  int32_t upd_parts;         //   upd_parts blocks (0: the launch is all of them)
   const float* Gy;           // KP x KP float32, G(Y) minus its mean entry
   float* gram_part;          // [gridDim.x][2][KP][KP]
   double* sc_part;           // [gridDim.x][4]: trace, pg, nonfinite, waits given up

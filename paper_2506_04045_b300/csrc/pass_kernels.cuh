@@ -614,16 +614,19 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
 
 // Split iteration, step 3: the row-local update (extrapolation, y G, step,
 // projection, writes, Gram and scalar partials) over rows in index order,
-// block b taking rows [b n / grid, (b+1) n / grid) and partial slot b.
+// block b taking rows [b n / parts, (b+1) n / parts) and partial slot b
+// (b = upd_block0 + blockIdx.x; parts = upd_parts, or the grid).
 template <int KP, bool MIXED>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) update_kernel(PassArgs a) {
   volatile FistaState* vs = a.st;
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
-  const int64_t p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
-  const int64_t p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  const int parts = a.upd_parts > 0 ? a.upd_parts : (int)gridDim.x;
+  const int b = a.upd_block0 + (int)blockIdx.x;
+  const int64_t p0 = a.n * (int64_t)b / parts;
+  const int64_t p1 = a.n * (int64_t)(b + 1) / parts;
   extern __shared__ __align__(16) float smem[];
-  pass_range<KP, MIXED, false, true>(a, pass, p0, p1, blockIdx.x, smem);
+  pass_range<KP, MIXED, false, true>(a, pass, p0, p1, b, smem);
 }
 
 // Partial products of chunked (very high degree) rows: hv_part[c] = sum over
@@ -670,7 +673,9 @@ struct FoldArgs {
   int32_t eval;             // 1: objective-only pass (Gram of the evaluated iterate only)
   int32_t eval_init;        // 1: also seed the solver (G(Y^1) = Gram of Xbar^0, gram2_cur)
   int32_t pad_;
-  unsigned long long* work; // spmm work counter, reset for the next pass (may be null)
+  unsigned long long* work; // spmm work counters, reset for the next pass (may be null)
+  int32_t n_work;           // how many (one per gather launch of a pass)
+  int32_t pad2_;
   double* A;                // KP x KP float64: Gram of the newest iterate (scratch)
   double* G;                // KP x KP float64: Gram of the next extrapolated point (scratch)
   float* Gy;                // KP x KP float32 for the next pass
@@ -853,7 +858,8 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   }
   if (tid == 0) {
     st->ticket = 0u;
-    if (f.work) *f.work = 0ull;
+    if (f.work)
+      for (int w = 0; w < f.n_work; ++w) f.work[w] = 0ull;
   }
 }
 

@@ -93,6 +93,17 @@ struct KPOps {
     else if (mixed) heavy_kernel<KP, true, false><<<grid, L::NT, 0, s>>>(a);
     else heavy_kernel<KP, false, false><<<grid, L::NT, 0, s>>>(a);
   }
+  // first gather unit whose rows all lie at positions >= r (units: chunk units
+  // of hub rows, then row units of TPW * kRowsPerUnit positions from n_heavy)
+  static int64_t unit_of_position(bool mixed, int64_t r, int64_t n_heavy, int64_t n_chunks) {
+    const int64_t cu = mixed ? spmm_chunk_units<KP, true>(n_chunks) : spmm_chunk_units<KP, false>(n_chunks);
+    const int64_t per = (int64_t)(mixed ? WLay<KP, true>::TPW : WLay<KP, false>::TPW) * kRowsPerUnit;
+    const int64_t q = std::max<int64_t>(r, n_heavy) - n_heavy;
+    return cu + (q + per - 1) / per;
+  }
+  static int64_t units(bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks) {
+    return mixed ? spmm_units<KP, true>(n, n_heavy, n_chunks) : spmm_units<KP, false>(n, n_heavy, n_chunks);
+  }
   static int occ_spmm(bool mixed) {
     int occ = 0;
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_kernel<KP, true>, L::NT, 0);
@@ -210,6 +221,16 @@ static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, boo
   FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static int64_t kp_unit_of_position(int KP, bool mixed, int64_t r, int64_t n_heavy, int64_t n_chunks) {
+  int64_t u = 0;
+  FC_DISPATCH(KP, u = Ops::unit_of_position(mixed, r, n_heavy, n_chunks));
+  return u;
+}
+static int64_t kp_units(int KP, bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks) {
+  int64_t u = 0;
+  FC_DISPATCH(KP, u = Ops::units(mixed, n, n_heavy, n_chunks));
+  return u;
+}
 static int kp_occ_spmm(int KP, bool mixed) {
   int o = 1;
   FC_DISPATCH(KP, o = Ops::occ_spmm(mixed));
@@ -302,12 +323,19 @@ static void l2_setaside_release() {
   }
 }
 
+// overlapped pass: minimum rows, and update blocks per resident update block
+static const int64_t kOvlMinRows = 1 << 20;
+static const int kOvlBlockFactor = 4;
+
 void ctx_free(cluster_ctx* c) {
   if (!c) return;
   for (cudaGraphExec_t g : c->graph_exec)
     if (g) cudaGraphExecDestroy(g);
   if (c->l2_window_bytes) l2_setaside_release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  for (cudaEvent_t e : c->ovl_ev)
+    if (e) cudaEventDestroy(e);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
                   c->A[1], c->Gy, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work, c->perm, c->inv};
@@ -338,6 +366,10 @@ PassArgs make_pass_args(const cluster_ctx* c, bool eval_exact) {
   a.Z0 = c->Z[0];
   a.Z1 = c->Z[1];
   a.work = c->work;
+  a.unit_lo = 0;
+  a.unit_hi = -1;
+  a.upd_block0 = 0;
+  a.upd_parts = 0;
   a.Gy = c->Gy;
   a.gram_part = c->gram_part;
   a.sc_part = c->sc_part;
@@ -356,6 +388,7 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
   f.sc_part = c->sc_part;
   f.parts = (!eval && c->split) ? c->parts_upd : c->parts;
   f.work = (!eval && c->split) ? c->work : nullptr;
+  f.n_work = (!eval && c->split) ? c->n_work : 0;
   f.eval = eval;
   f.eval_init = eval_init;
   f.A = c->A[0];
@@ -367,9 +400,45 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
 // Enqueue one iteration (heavy chunks, fused pass, fold).
 // One pass; `parity` is the pass counter's parity when it runs (it selects
 // the iterate buffer the gather reads and so the L2 window).
+// Overlapped split pass: gather chunk ch on s (hub-row sums after the first),
+// then the update of row chunk ch on the side stream, which waits only for
+// the gathers so far; the caller's stream waits for the last update.
+// tev (profiling, may be null): [0], [1] after the last gather, [2] after the join.
+static void enqueue_split_ovl(const cluster_ctx* c, cudaStream_t s, int parity, cudaEvent_t* tev) {
+  const PassArgs a = make_pass_args(c, false);
+  void* win = c->mixed ? (void*)c->XS[parity & 1] : (void*)c->X[parity & 1];
+  for (int ch = 0; ch < c->ovl; ++ch) {
+    PassArgs g = a;
+    g.unit_lo = c->ovl_units[ch];
+    g.unit_hi = c->ovl_units[ch + 1];
+    g.work = c->work + ch;
+    if (g.unit_hi > g.unit_lo) {
+      if (c->l2_window_bytes) kp_launch_spmm_window(c->KP, g, c->spmm_grid_ovl, c->mixed, s, win, c->l2_window_bytes);
+      else kp_launch_spmm(c->KP, g, c->spmm_grid_ovl, c->mixed, s);
+    }
+    if (ch == 0 && c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
+    if (tev && ch + 1 == c->ovl) {
+      cudaEventRecord(tev[0], s);
+      cudaEventRecord(tev[1], s);
+    }
+    cudaEventRecord(c->ovl_ev[ch], s);
+    cudaStreamWaitEvent(c->side_stream, c->ovl_ev[ch], 0);
+    PassArgs u = a;
+    u.upd_block0 = c->ovl_blocks[ch];
+    u.upd_parts = c->parts_upd;
+    const int nb = c->ovl_blocks[ch + 1] - c->ovl_blocks[ch];
+    if (nb > 0) kp_launch_update(c->KP, u, nb, c->mixed, c->tc_update, c->side_stream);
+  }
+  cudaEventRecord(c->ovl_ev[c->ovl], c->side_stream);
+  cudaStreamWaitEvent(s, c->ovl_ev[c->ovl], 0);
+  if (tev) cudaEventRecord(tev[2], s);
+}
+
 static void enqueue_pass(const cluster_ctx* c, cudaStream_t s, int parity) {
   PassArgs a = make_pass_args(c, false);
-  if (c->split) {
+  if (c->split && c->ovl > 0) {
+    enqueue_split_ovl(c, s, parity, nullptr);
+  } else if (c->split) {
     if (c->l2_window_bytes)
       kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
                             c->mixed ? (void*)c->XS[parity & 1] : (void*)c->X[parity & 1], c->l2_window_bytes);
@@ -465,7 +534,8 @@ static cluster_status capture_graph(cluster_ctx* c) {
     FC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < c->graph_chunk; ++i) enqueue_pass(c, c->cap_stream, p0 + i);
     FC_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&c->graph_exec[p0], g, 0);
+    // node priorities: the overlapped update launches come from a high-priority stream
+    cudaError_t e = cudaGraphInstantiate(&c->graph_exec[p0], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
       set_error("graph instantiate: %s", cudaGetErrorString(e));
@@ -640,6 +710,48 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->row_cost = 6;
   FC_TRY(build_schedule(c));
 
+  // Overlapped pass: with the internal numbering the gather order is the
+  // identity, so a prefix of the gather's units is a prefix of the rows and
+  // the update of a row chunk can start once that prefix is gathered.  Eligible
+  // contexts use kOvlBlockFactor times more (smaller) update blocks, with or
+  // without the overlap, so that both schedules sum the same partials (same
+  // bits) and the last chunk's update is short.
+  if (c->split && c->relabeled && n >= kOvlMinRows) {
+    int* dflag = nullptr;
+    int hflag = 1;
+    FC_CUDA(cudaMalloc(&dflag, sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+      order_identity_kernel<<<grid_for(n), 256, 0, s>>>(c->order, n, dflag);
+      e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dflag);
+    if (e != cudaSuccess) {
+      set_error("order check: %s", cudaGetErrorString(e));
+      return CLUSTER_ECUDA;
+    }
+    if (hflag == 0) {
+      c->ovl_eligible = true;
+      c->parts_upd = (int)std::min<int64_t>((int64_t)c->parts_upd * kOvlBlockFactor, tiles);
+      if (opt.overlap) {
+        c->ovl = cluster_ctx::kMaxOvl;
+        c->n_work = c->ovl;
+        c->spmm_grid_ovl = sms * std::max(1, kp_occ_spmm(c->KP, c->mixed) - 1);
+        for (int ch = 0; ch <= c->ovl; ++ch) c->ovl_blocks[ch] = (int)((int64_t)ch * c->parts_upd / c->ovl);
+        c->ovl_units[0] = 0;
+        for (int ch = 1; ch < c->ovl; ++ch)
+          c->ovl_units[ch] = kp_unit_of_position(c->KP, c->mixed, n * (int64_t)c->ovl_blocks[ch] / c->parts_upd,
+                                                 c->n_heavy, c->n_chunks);
+        c->ovl_units[c->ovl] = kp_units(c->KP, c->mixed, n, c->n_heavy, c->n_chunks);
+        int prio_lo = 0, prio_hi = 0;
+        FC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        FC_CUDA(cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, prio_hi));
+        for (int ch = 0; ch <= c->ovl; ++ch) FC_CUDA(cudaEventCreateWithFlags(&c->ovl_ev[ch], cudaEventDisableTiming));
+      }
+    }
+  }
+
   // iterate buffers and reductions
   const size_t nk = (size_t)n * c->KP;
   FC_CUDA(cudaMalloc(&c->X[0], sizeof(float) * nk));
@@ -649,8 +761,8 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     FC_CUDA(cudaMalloc(&c->Z[1], sizeof(float) * nk));
     FC_CUDA(cudaMemsetAsync(c->Z[0], 0, sizeof(float) * nk, s));
     FC_CUDA(cudaMemsetAsync(c->Z[1], 0, sizeof(float) * nk, s));
-    FC_CUDA(cudaMalloc(&c->work, sizeof(unsigned long long)));
-    FC_CUDA(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), s));
+    FC_CUDA(cudaMalloc(&c->work, sizeof(unsigned long long) * cluster_ctx::kMaxOvl));
+    FC_CUDA(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long) * cluster_ctx::kMaxOvl, s));
   } else {
     FC_CUDA(cudaMalloc(&c->Zp, sizeof(float) * nk));
     FC_CUDA(cudaMemsetAsync(c->Zp, 0, sizeof(float) * nk, s));
@@ -828,6 +940,7 @@ extern "C" void cluster_options_default(cluster_options* opt) {
   opt->relabel = 1;
   opt->l2_window = 1;
   opt->update_engine = 0;
+  opt->overlap = 0;
 }
 
 extern "C" const char* cluster_last_error(void) { return g_err.c_str(); }
@@ -888,7 +1001,11 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
   for (int64_t i = 0; i < iters; ++i) {
     cudaEvent_t* e = &ev[(size_t)(5 * i)];
     cudaEventRecord(e[0], s);
-    if (c->split) {
+    if (c->split && c->ovl > 0) {
+      // overlapped: pass = start to the last gather (hub-row sums included),
+      // update = the part of the updates after the last gather
+      enqueue_split_ovl(c, s, (int)((c->pass_guess + i) & 1), &e[1]);
+    } else if (c->split) {
       const int par = (int)((c->pass_guess + i) & 1);
       if (c->l2_window_bytes)
         kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
@@ -945,6 +1062,21 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
   out->fold_ms = tf / iters;
   out->update_ms = tu / iters;
   out->launches = iters;
+  {
+    // launches per iteration: split = gather(s) + update(s) + chunk sums (if any) + fold;
+    // fused = chunk partials (if any) + pass + fold; plus the limit kernel
+    int64_t per = 0;
+    if (c->split && c->ovl > 0) {
+      for (int ch = 0; ch < c->ovl; ++ch)
+        per += (c->ovl_units[ch + 1] > c->ovl_units[ch] ? 1 : 0) + (c->ovl_blocks[ch + 1] > c->ovl_blocks[ch] ? 1 : 0);
+      per += (c->n_heavy > 0 ? 1 : 0) + 1;
+    } else if (c->split) {
+      per = 3 + (c->n_heavy > 0 ? 1 : 0);
+    } else {
+      per = 2 + (c->n_chunks > 0 ? 1 : 0);
+    }
+    out->kernels = 1 + per * iters;
+  }
   out->heavy_rows = c->n_heavy;
   out->heavy_nnz = c->heavy_nnz;
   return CLUSTER_OK;

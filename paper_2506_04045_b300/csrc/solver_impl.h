@@ -53,6 +53,19 @@ struct cluster_ctx {
   int parts_upd = 1;                    // blocks (and partial slots) of the update kernel
   bool tc_update = true;                // update on tcgen05 where the kernel exists (k <= 32)
   int spmm_grid = 1;
+  // overlapped pass (opt.overlap): row chunk c's update runs on side_stream
+  // once the gather units that cover its rows (ovl_units[c+1]) are done, while
+  // the next chunks are gathered; the update blocks and partial slots are the
+  // unchunked launch's (ovl_blocks), so no value changes
+  static constexpr int kMaxOvl = 8;
+  int ovl = 0;                          // chunks (0: one gather and one update launch)
+  bool ovl_eligible = false;            // relabeled, identity gather order, n >= kOvlMinRows
+  int spmm_grid_ovl = 1;                // gather grid beside one update block per SM
+  int n_work = 1;                       // gather work counters in use (one per gather launch)
+  int64_t ovl_units[kMaxOvl + 1] = {};
+  int ovl_blocks[kMaxOvl + 1] = {};
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ovl_ev[kMaxOvl + 1] = {};
   double* A[2] = {nullptr, nullptr};  // float64 fold scratch: Gram of Xbar^n, Gram of Y^{n+1}
   float* Gy = nullptr;                 // float32 G(Y) (minus its mean) read by the next pass
   float* gram_part = nullptr;

@@ -7,7 +7,8 @@
 namespace fc {
 
 // Split iteration, step 1: z_i = (S Xbar^{pass})_i for every row, stored in
-// Z_{(pass+1)&1}, plus the partial products of chunked rows.  Pure gather, no
+// Z_{(pass+1)&1}, plus the partial products of chunked rows (units
+// [unit_lo, unit_hi) of the work list when the pass is chunked).  Pure gather, no
 // per-tile barrier: warps take work units from a global counter (units of
 // TPW chunks first, then units of TPW * kRowsPerUnit consecutive positions of
 // the processing order, whose neighbouring positions hold rows of similar
@@ -83,13 +84,14 @@ __global__ void __launch_bounds__(Lay<KP>::NT, spmm_min_blocks<KP, MIXED>()) spm
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
   const int lane = threadIdx.x & 31;
-  const int64_t units = spmm_units<KP, MIXED>(a.n, a.n_heavy, a.n_chunks);
+  const int64_t units = a.unit_hi < 0 ? spmm_units<KP, MIXED>(a.n, a.n_heavy, a.n_chunks) : a.unit_hi;
   for (;;) {
     unsigned long long u = 0;
     if (lane == 0) u = atomicAdd(a.work, 1ull);
     u = __shfl_sync(kFull, u, 0);
-    if ((int64_t)u >= units) break;
-    spmm_unit<KP, MIXED>(a, pass, (int64_t)u, lane);
+    const int64_t unit = a.unit_lo + (int64_t)u;
+    if (unit >= units) break;
+    spmm_unit<KP, MIXED>(a, pass, unit, lane);
   }
 }
 

@@ -467,22 +467,24 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
   // first barrier, which every thread reaches after tid 0 has read them
 }
 
-// Split iteration, step 3, for KP = 32: block b takes rows
-// [b n / grid, (b+1) n / grid) and partial slot b (as update_kernel).
+// Split iteration, step 3, for KP = 32: block b = upd_block0 + blockIdx.x takes
+// rows [b n / parts, (b+1) n / parts) and partial slot b (as update_kernel).
 template <int KP, bool MIXED>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) update_tc_kernel(PassArgs a) {
   volatile FistaState* vs = a.st;
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
-  const int64_t p0 = a.n * (int64_t)blockIdx.x / gridDim.x;
-  const int64_t p1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  const int parts = a.upd_parts > 0 ? a.upd_parts : (int)gridDim.x;
+  const int blk = a.upd_block0 + (int)blockIdx.x;
+  const int64_t p0 = a.n * (int64_t)blk / parts;
+  const int64_t p1 = a.n * (int64_t)(blk + 1) / parts;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   __shared__ uint64_t bars[2];
   __shared__ uint32_t tslot;
   __shared__ int tmo_flag[2];
   TcBlock b;
   tc_begin<KP>(b, tc_smem_raw, bars, &tslot, tmo_flag);
-  tc_update_range<KP, MIXED>(a, pass, p0, p1, blockIdx.x, b);
+  tc_update_range<KP, MIXED>(a, pass, p0, p1, blk, b);
   tc_end<KP>(b);
 }
 

@@ -44,7 +44,7 @@ def test_options_defaults():
     o = pkg.default_options()
     assert (o.precision, o.step_rule, o.stop_rule, o.accel, o.borrow, o.validate) == (0, 1, 0, 1, 0, 1)
     assert o.tau == 1.0 and o.tol == 0.0 and o.max_iter == 1000 and o.graph_chunk == 16
-    assert o.fused_pass == 0 and o.relabel == 1 and o.l2_window == 1 and o.update_engine == 0
+    assert o.fused_pass == 0 and o.relabel == 1 and o.l2_window == 1 and o.update_engine == 0 and o.overlap == 0
 
 
 def test_init_argument_errors_are_status_codes():
