@@ -130,6 +130,11 @@ __device__ __forceinline__ void ld16x16(uint32_t taddr, float* v) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
 __device__ __forceinline__ int sw_chunk(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
 
@@ -346,6 +351,17 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
     }
   }
   for (uint32_t it = 0; it < ntiles; ++it) {
+    // the next tile's rows (4 arrays of up to 32 consecutive rows) into L2, a
+    // tile ahead of their loads
+    if (tid == 0 && it + 1 < ntiles) {
+      const int64_t r0 = p0 + (int64_t)(it + 1) * L::R;
+      const int64_t rows = (p1 - r0 < L::R) ? p1 - r0 : L::R;
+      const uint32_t bytes = (uint32_t)(rows * KP * sizeof(float));
+      tc::prefetch_l2(Zcur + r0 * KP, bytes);
+      tc::prefetch_l2(P + r0 * KP, bytes);
+      tc::prefetch_l2(Qx + r0 * KP, bytes);
+      tc::prefetch_l2(Zprv + r0 * KP, bytes);
+    }
     // y G of this tile -> staging rows
     wait_bar(b.bar_yg, ph0 + it);
     if (qd < 2 && !dead) {
