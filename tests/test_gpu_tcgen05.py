@@ -93,3 +93,41 @@ def test_wait_that_gives_up_is_a_status_and_the_context_survives():
     s2.step(3)
     assert torch.equal(s2.get_U(), U3)
     s2.close()
+
+
+# a single partial tile (n = 5), one row past a tile (n = 33), fewer rows than
+# update blocks, and a few full tiles with a ragged one
+@pytest.mark.parametrize("n", [5, 33, 97, 1000])
+def test_tcgen05_update_small_and_ragged_n(n):
+    spec = synth.GraphSpec("dcsbm", n, 32, 300 + n, mean_deg=min(12.0, n / 2.0))
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(n, 32, 300 + n, device="cuda")
+    Ut, rt = _run(rp, c, v, U0, 30, update_engine=0)
+    Uw, rw = _run(rp, c, v, U0, 30, update_engine=1)
+    assert torch.equal(Ut, Uw)
+    assert rt["f"] == rw["f"] and rt["pg_norm"] == rw["pg_norm"]
+    S = to_scipy(rp, c, v, n)
+    o = oracle.fista(S, U0.cpu().numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=30, stop="none")
+    assert maxabs(Ut.cpu().numpy(), o.U) <= 1e-5
+    # f = ||S||^2 - 2 sum_i p_i + ||A||^2: float32 sums of terms of size ||S||^2, so
+    # the error bound scales with ||S||^2 (f itself can be far smaller)
+    s2 = float((v.double() ** 2).sum())
+    assert abs(rt["f"] - o.losses[rt["f_iter"]]) <= 1e-6 * max(abs(o.losses[rt["f_iter"]]), s2)
+
+
+def test_tcgen05_update_with_a_stop_rule_inside_a_graph():
+    # the relative PG rule fires inside a captured graph: the passes after it
+    # return at once and both engines stop at the same iteration with the same bits
+    spec = synth.GraphSpec("dcsbm", 6000, 20, 333, mean_deg=15.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, 20, 333, device="cuda")
+    outs = []
+    for eng in (0, 1):
+        s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_PG_REL, tol=0.5, max_iter=400, update_engine=eng)
+        rep = s.solve()
+        outs.append((s.get_U(), rep))
+        s.close()
+    (Ut, rt), (Uw, rw) = outs
+    assert rt["done"] == rw["done"] == 1 and rt["status"] == rw["status"] == pkg.OK
+    assert rt["out_iter"] == rw["out_iter"] < 400
+    assert torch.equal(Ut, Uw)
