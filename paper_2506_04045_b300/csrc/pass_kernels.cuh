@@ -863,6 +863,50 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   }
 }
 
+// Gram partials of one iterate buffer without any product with S (the solver's
+// start: G(Y^1) = Xbar^0^T Xbar^0 and ||Xbar^0^T Xbar^0||^2; the loss of Xbar^0
+// comes from the first pass, whose product with S forms its trace term).
+// Block b takes rows [b n / grid, (b+1) n / grid) in tiles of 32 staged in
+// shared memory; thread t owns entries t, t + 256, ... of the KP x KP matrix,
+// sums each tile in float32 and the tiles in float64, and writes the block's
+// partial into gram_part[b][0] (sc_part[b] = 0: no trace term).
+template <int KP>
+__global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X, int64_t n, float* gram_part,
+                                                    double* sc_part) {
+  static_assert(KP <= 64, "per-thread entries");
+  constexpr int E2 = KP * KP, EPT = (E2 + 255) / 256, TR = 32;
+  __shared__ float tile[TR * KP];
+  const int tid = threadIdx.x;
+  const int64_t p0 = n * (int64_t)blockIdx.x / gridDim.x, p1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  double acc[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) acc[q] = 0.0;
+  for (int64_t base = p0; base < p1; base += TR) {
+    const int rows = (int)((p1 - base < TR) ? p1 - base : TR);
+    for (int e = tid; e < TR * KP; e += 256) tile[e] = (e / KP < rows) ? X[base * KP + e] : 0.0f;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * 256;
+      if (e < E2) {
+        const int i = e / KP, j = e % KP;
+        float t = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < TR; ++r) t = fmaf(tile[r * KP + i], tile[r * KP + j], t);
+        acc[q] += (double)t;
+      }
+    }
+    __syncthreads();
+  }
+  float* go = gram_part + (size_t)blockIdx.x * 2 * E2;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * 256;
+    if (e < E2) go[e] = (float)acc[q];
+  }
+  if (tid < 4) sc_part[blockIdx.x * 4 + tid] = 0.0;
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256) fold_kernel(FoldArgs f) {
   fold_body<KP>(f, blockIdx.x, gridDim.x);

@@ -179,6 +179,9 @@ struct KPOps {
     if (mixed) update_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
     else update_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
   }
+  static void launch_gram0(const float* X, int64_t n, float* gp, double* sp, int grid, cudaStream_t s) {
+    if constexpr (KP <= 64) gram0_kernel<KP><<<grid, 256, 0, s>>>(X, n, gp, sp);
+  }
   static void launch_fold(const FoldArgs& f, cudaStream_t s) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
     fold_kernel<KP><<<(nent + fold_epb<KP>() - 1) / fold_epb<KP>(), 256, 0, s>>>(f);
@@ -221,6 +224,9 @@ static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, boo
   FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static void kp_launch_gram0(int KP, const float* X, int64_t n, float* gp, double* sp, int grid, cudaStream_t s) {
+  FC_DISPATCH(KP, Ops::launch_gram0(X, n, gp, sp, grid, s));
+}
 static int64_t kp_unit_of_position(int KP, bool mixed, int64_t r, int64_t n_heavy, int64_t n_chunks) {
   int64_t u = 0;
   FC_DISPATCH(KP, u = Ops::unit_of_position(mixed, r, n_heavy, n_chunks));
@@ -802,17 +808,27 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   h.accel = opt.accel ? 1 : 0;
   h.k = k;
   FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
-  // Gram of Xbar^0 and f(Xbar^0): seeds G(Y^1) = Xbar^0^T Xbar^0
-  enqueue_eval(c, 0, 1, s);
-  FC_CUDA(cudaGetLastError());
-  FC_TRY(read_state(c));
-  h = c->host_st;
-  h.loss_last = h.eval_f;
-  h.trace_last = h.eval_trace;
-  h.gram2_last = h.eval_gram2;
-  h.f_iter = 0;
-  FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
-  FC_CUDA(cudaStreamSynchronize(s));
+  // Gram of Xbar^0: seeds G(Y^1) = Xbar^0^T Xbar^0 and ||Xbar^0^T Xbar^0||^2.  For
+  // k <= 64 without a product with S: the first pass's product gives the trace
+  // term of f(Xbar^0), and its fold the loss (f_iter stays -1 until then).
+  // k = 128: one objective-only pass (also f(Xbar^0) at once).
+  if (c->KP <= 64) {
+    kp_launch_gram0(c->KP, c->X[0], n, c->gram_part, c->sc_part, c->parts, s);
+    kp_launch_fold(c->KP, make_fold_args(c, 1, 1), s);
+    FC_CUDA(cudaGetLastError());
+    FC_TRY(read_state(c));
+  } else {
+    enqueue_eval(c, 0, 1, s);
+    FC_CUDA(cudaGetLastError());
+    FC_TRY(read_state(c));
+    h = c->host_st;
+    h.loss_last = h.eval_f;
+    h.trace_last = h.eval_trace;
+    h.gram2_last = h.eval_gram2;
+    h.f_iter = 0;
+    FC_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(FistaState), cudaMemcpyHostToDevice, s));
+    FC_CUDA(cudaStreamSynchronize(s));
+  }
   c->pass_guess = 0;
   // persisting L2 window over the gathered rows of the highest-degree
   // articles (the first rows in the internal numbering): half of the
