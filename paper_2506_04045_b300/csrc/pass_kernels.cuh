@@ -867,24 +867,39 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
 // start: G(Y^1) = Xbar^0^T Xbar^0 and ||Xbar^0^T Xbar^0||^2; the loss of Xbar^0
 // comes from the first pass, whose product with S forms its trace term).
 // Block b takes rows [b n / grid, (b+1) n / grid) in tiles of 32 staged in
-// shared memory; thread t owns entries t, t + 256, ... of the KP x KP matrix,
-// sums each tile in float32 and the tiles in float64, and writes the block's
-// partial into gram_part[b][0] (sc_part[b] = 0: no trace term).
+// shared memory, the next tile's loads in flight while a tile is summed;
+// thread t owns entries t, t + 256, ... of the KP x KP matrix, sums each tile
+// in float32 and the tiles in float64, and writes the block's partial into
+// gram_part[b][0] (sc_part[b] = 0: no trace term).
 template <int KP>
 __global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X, int64_t n, float* gram_part,
                                                     double* sc_part) {
   static_assert(KP <= 64, "per-thread entries");
-  constexpr int E2 = KP * KP, EPT = (E2 + 255) / 256, TR = 32;
+  constexpr int E2 = KP * KP, EPT = (E2 + 255) / 256, TR = 32, LPT = TR * KP / 256;
+  static_assert(LPT * 256 == TR * KP || KP < 8, "tile loads per thread");
+  constexpr int LP = LPT > 0 ? LPT : 1;
   __shared__ float tile[TR * KP];
   const int tid = threadIdx.x;
   const int64_t p0 = n * (int64_t)blockIdx.x / gridDim.x, p1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
   double acc[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) acc[q] = 0.0;
+  // element e of the tile at row base: X[base KP + e] for rows below p1, else 0
+  auto fetch = [&](int64_t base, float* v) {
+#pragma unroll
+    for (int l = 0; l < LP; ++l) {
+      const int e = tid + l * 256;
+      v[l] = (e < TR * KP && base + e / KP < p1) ? __ldg(X + base * KP + e) : 0.0f;
+    }
+  };
+  float nxt[LP];
+  if (p0 < p1) fetch(p0, nxt);
   for (int64_t base = p0; base < p1; base += TR) {
-    const int rows = (int)((p1 - base < TR) ? p1 - base : TR);
-    for (int e = tid; e < TR * KP; e += 256) tile[e] = (e / KP < rows) ? X[base * KP + e] : 0.0f;
+#pragma unroll
+    for (int l = 0; l < LP; ++l)
+      if (tid + l * 256 < TR * KP) tile[tid + l * 256] = nxt[l];
     __syncthreads();
+    if (base + TR < p1) fetch(base + TR, nxt);
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * 256;

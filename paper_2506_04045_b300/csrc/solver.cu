@@ -813,8 +813,13 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   // term of f(Xbar^0), and its fold the loss (f_iter stays -1 until then).
   // k = 128: one objective-only pass (also f(Xbar^0) at once).
   if (c->KP <= 64) {
-    kp_launch_gram0(c->KP, c->X[0], n, c->gram_part, c->sc_part, c->parts, s);
-    kp_launch_fold(c->KP, make_fold_args(c, 1, 1), s);
+    // as many blocks as partial slots, up to 8 resident per SM, at least a tile each
+    const int slots = std::max(c->parts, c->parts_upd);
+    const int g0 = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)slots, (int64_t)sms * 8, (n + 31) / 32}));
+    kp_launch_gram0(c->KP, c->X[0], n, c->gram_part, c->sc_part, g0, s);
+    FoldArgs f0 = make_fold_args(c, 1, 1);
+    f0.parts = g0;
+    kp_launch_fold(c->KP, f0, s);
     FC_CUDA(cudaGetLastError());
     FC_TRY(read_state(c));
   } else {
