@@ -335,7 +335,9 @@ CLUSTER_API cluster_status cluster_batch_step(cluster_batch* b, int64_t iters, c
  * the CUDA graph is re-captured with the chosen shapes. */
 CLUSTER_API cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trials);
 
-/* JSON description of the batch's classes and launch shapes into buf. */
+/* JSON description of the batch's classes and launch shapes into buf (after
+ * cluster_batch_autotune also each class's gather and update times for the
+ * chosen shapes, the class running alone, in milliseconds). */
 CLUSTER_API cluster_status cluster_batch_describe(cluster_batch* b, char* buf, size_t len);
 
 /* Copy instance i's output iterate into U_out (device, n_i x k_i). */

@@ -42,6 +42,7 @@ struct BatchClass {
   int occ_spmm = 1, occ_upd = 1;   // resident blocks per SM of the two persistent kernels
   int64_t gather_blocks_max = 1;   // blocks beyond this would find no gather unit
   bool tuned = false;
+  double gather_ms = 0.0, update_ms = 0.0;  // autotune: the chosen shapes' best times (class alone)
   BatchMeta meta{};
 };
 
@@ -457,6 +458,7 @@ extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trial
               if (mn < best) {
                 best = mn;
                 best_s[ci] = (int)std::min<int64_t>((int64_t)sms * (c2 + 1), bc.gather_blocks_max);
+                bc.gather_ms = mn;
               }
             }
           }
@@ -471,6 +473,7 @@ extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trial
               if (mn < best) {
                 best = mn;
                 best_u[ci] = std::max(1, std::min(sms * ((int)c2 + 1), bc.n_items));
+                bc.update_ms = mn;
               }
             }
           }
@@ -499,9 +502,10 @@ extern "C" cluster_status cluster_batch_describe(cluster_batch* b, char* buf, si
     char tmp[512];
     snprintf(tmp, sizeof(tmp),
              "%s{\"kp\": %d, \"mixed\": %d, \"instances\": %zu, \"gather_units\": %lld, \"chunked_rows\": %lld, "
-             "\"update_items\": %d, \"gather_blocks\": %d, \"update_blocks\": %d, \"tuned\": %d}",
+             "\"update_items\": %d, \"gather_blocks\": %d, \"update_blocks\": %d, \"tuned\": %d, "
+             "\"gather_ms\": %.4f, \"update_ms\": %.4f}",
              ci ? ", " : "", bc.KP, bc.mixed ? 1 : 0, bc.members.size(), (long long)bc.units, (long long)bc.heavy,
-             bc.n_items, bc.spmm_grid, bc.upd_grid, bc.tuned ? 1 : 0);
+             bc.n_items, bc.spmm_grid, bc.upd_grid, bc.tuned ? 1 : 0, bc.gather_ms, bc.update_ms);
     out += tmp;
   }
   out += "]}";

@@ -329,6 +329,8 @@ static void l2_setaside_release() {
   }
 }
 
+// update blocks: at least this many tiles each (see init_impl)
+static const int64_t kMinTilesPerBlock = 32;
 // overlapped pass: minimum rows, and update blocks per resident update block
 static const int64_t kOvlMinRows = 1 << 20;
 static const int kOvlBlockFactor = 4;
@@ -702,6 +704,12 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     FC_CUDA(kp_setup_update_attr(c->KP));
     c->spmm_grid = sms * kp_occ_spmm(c->KP, c->mixed);
     int64_t pu = (int64_t)sms * kp_occ_update(c->KP, c->mixed, c->tc_update);
+    // at least kMinTilesPerBlock tiles per update block, but not fewer blocks
+    // than SMs: a batch runs every block's row range as a work item of its own
+    // (setting up G(Y), writing a 2 x KP x KP partial that the fold reads back),
+    // so tiny ranges cost more in set-up than in rows, while a lone small solve
+    // still keeps every SM busy
+    pu = std::min<int64_t>(pu, std::max<int64_t>((int64_t)sms, tiles / kMinTilesPerBlock));
     if (pu > tiles) pu = tiles;
     c->parts_upd = (int)std::max<int64_t>(1, pu);
   }
