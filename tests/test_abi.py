@@ -97,3 +97,43 @@ def test_csr_builder_errors():
     assert ei.value.status == pkg.EINVAL
     with pytest.raises(pkg.ClusterError):
         pkg.csr_from_edges(3, [0], [1], [np.inf])
+
+
+def test_ctypes_structs_match_the_c_header():
+    # the binding's ctypes mirrors of the header's structs: same size, and every
+    # named field at the same offset (a field added on one side only would shift
+    # the ones after it and pass garbage through the ABI)
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2506_04045_b300 import binding as b
+    pairs = {"cluster_csr": b.CSR, "cluster_options": b.Options, "cluster_report": b.Report,
+             "cluster_kernel_times": b.KernelTimes, "cluster_server_options": b.ServerOptions,
+             "cluster_server_stats": b.ServerStats, "cluster_request_times": b.RequestTimes}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cluster.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            if not fname.startswith("_"):
+                lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with tempfile.TemporaryDirectory() as td:
+        src, exe = os.path.join(td, "layout.c"), os.path.join(td, "layout")
+        with open(src, "w") as fh:
+            fh.write("\n".join(lines) + "\n")
+        subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), src, "-o", exe], check=True,
+                       capture_output=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        cname, field, val = ln.split()
+        got[(cname, field)] = int(val)
+    for cname, cls in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            if not fname.startswith("_"):
+                assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
