@@ -237,7 +237,9 @@ CLUSTER_API cluster_status cluster_get_U(cluster_ctx* ctx, float* U_out);
 
 /* f(U) = ||S||_F^2 + ||U^T U||_F^2 - 2 sum_i <u_i, (S U)_i> in float64
  * (Sect. 3, "Loss Update"), for device S and U (n x k).  Allocates and frees
- * its own scratch; synchronises `stream`.  *f receives the value. */
+ * its own scratch; synchronises `stream`.  *f receives the value.  S is
+ * trusted, not validated (unlike cluster_init): a column index outside [0, n)
+ * or a decreasing row pointer makes the kernels read outside S's arrays. */
 CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, const float* U,
                                              void* stream, double* f);
 
@@ -255,11 +257,14 @@ CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, co
  * ordered by degree, so graphs with rows of very high degree run slower than
  * with cluster_objective.
  * The first call on a device looks up the scratch array's device address for
- * that device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array and each call resets what must
- * start at zero, so calls that overlap on the GPU (other threads, other
- * streams) race and must be serialised by the caller.  The call synchronises
- * `stream` and writes the value to *f. */
+ * that device (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not use
+ * the library across a cudaDeviceReset (the module is reloaded and the kept
+ * address goes stale).  All calls share the one array and each call resets
+ * what must start at zero, so calls that overlap on the GPU (other threads,
+ * other streams) race and must be serialised by the caller.  S is trusted as
+ * in cluster_objective (not validated).  The call synchronises `stream` and
+ * writes the value to *f. */
 CLUSTER_API cluster_status cluster_objective_static(const cluster_csr* S, int32_t k, const float* U,
                                                     void* stream, double* f);
 

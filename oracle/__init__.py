@@ -33,10 +33,12 @@ from .fista import (
     spectral_norm,
     momentum_factors,
     fista_step_rows,
+    gram_blocks,
 )
 
 __all__ = [
     "frob2", "objective_dense", "objective_trace", "gradient_matrix", "gradient_columns",
     "hessian_apply", "hessian_apply_sparse", "curvature", "slope", "duchi", "project_omega", "lipschitz", "gpa", "fista",
     "OracleResult", "csr_from_edges", "spectral_norm", "momentum_factors", "fista_step_rows",
+    "gram_blocks",
 ]

@@ -204,6 +204,7 @@ class OracleResult:
     losses: list                   # losses evaluated in order (loss^0, loss^1, ...)
     pg_norms: list                 # ||Y^n - Xbar^n||_F / tau per iteration
     history: list = dataclasses.field(default_factory=list)   # iterates, if requested
+    t_values: list = dataclasses.field(default_factory=list)  # FISTA: t_1, t_2, ... as used
 
 
 def gpa(S, U0, tau: float, tol: float = 0.0, max_iter: int = 100,
@@ -273,6 +274,7 @@ def fista(S, U0, tau: float, tol: float = 0.0, max_iter: int = 100,
     loss_prev = loss_of(Xbar_prev)
     losses, pgs, hist = [loss_prev], [], []
     t = 1.0
+    ts = [t]
     pg_first = None
     for it in range(1, max_iter + 1):
         share = X.T @ X
@@ -287,18 +289,19 @@ def fista(S, U0, tau: float, tol: float = 0.0, max_iter: int = 100,
         loss = loss_of(Xbar)
         losses.append(loss)
         if stop == "loss" and loss_prev - loss <= tol:
-            return OracleResult(Xbar, it, True, losses, pgs, hist)
+            return OracleResult(Xbar, it, True, losses, pgs, hist, ts)
         if stop == "pg_rel" and pg <= pg_tol * pg_first:
-            return OracleResult(Xbar, it, True, losses, pgs, hist)
+            return OracleResult(Xbar, it, True, losses, pgs, hist, ts)
         if stop == "pg_abs" and pg <= pg_tol:
-            return OracleResult(Xbar, it, True, losses, pgs, hist)
+            return OracleResult(Xbar, it, True, losses, pgs, hist, ts)
         t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
         beta = (t - 1.0) / t_next if accel else 0.0
         X = Xbar + beta * (Xbar - Xbar_prev)
         Xbar_prev = Xbar
         loss_prev = loss
         t = t_next
-    return OracleResult(Xbar_prev, max_iter, False, losses, pgs, hist)
+        ts.append(t)
+    return OracleResult(Xbar_prev, max_iter, False, losses, pgs, hist, ts)
 
 
 def momentum_factors(n_iter: int, accel: bool = True) -> list:
@@ -314,18 +317,41 @@ def momentum_factors(n_iter: int, accel: bool = True) -> list:
     return out
 
 
-def fista_step_rows(S, Xbar_cur, Xbar_prev, beta: float, tau: float, rows) -> np.ndarray:
+def gram_blocks(blocks, beta=None) -> np.ndarray:
+    """share = X^T X (Sect. 3; C x C with the paper's X) summed over row blocks
+    of X in float64, for iterates too large to hold whole: ``blocks`` yields
+    arrays of consecutive rows (any float dtype).  With ``beta`` each block is
+    a pair (rows of Xbar^n, the same rows of Xbar^{n-1}) and the rows of the
+    extrapolated point X^{n+1} = Xbar^n + beta (Xbar^n - Xbar^{n-1}) of
+    Algorithm 4 are summed."""
+    share = None
+    for B in blocks:
+        if beta is not None:
+            Bc = np.asarray(B[0], dtype=np.float64)
+            Bp = np.asarray(B[1], dtype=np.float64)
+            B = Bc + beta * (Bc - Bp)
+        B = np.asarray(B, dtype=np.float64)
+        g = B.T @ B
+        share = g if share is None else share + g
+    return share
+
+
+def fista_step_rows(S, Xbar_cur, Xbar_prev, beta: float, tau: float, rows, share=None) -> np.ndarray:
     """One iteration of Algorithm 4 evaluated only at the given articles.
 
     X = Xbar_cur + beta (Xbar_cur - Xbar_prev) (the extrapolated point),
     share = X^T X over all articles, then for each requested i:
     grad_i = -4 (X s_i - share x_i) and xbar_i = Algorithm 1 applied to
-    x_i - tau grad_i.  Returns the rows of the next Xbar (float64)."""
+    x_i - tau grad_i.  Returns the rows of the next Xbar (float64).  When the
+    arrays in hand hold only some articles (the requested rows and their
+    neighbours in S), ``share`` must be given: X^T X over all articles of the
+    extrapolated point (gram_blocks)."""
     S = _as_csr(S)
     Xc = np.asarray(Xbar_cur, dtype=np.float64)
     Xp = np.asarray(Xbar_prev, dtype=np.float64)
     X = Xc + beta * (Xc - Xp)
-    share = X.T @ X
+    if share is None:
+        share = X.T @ X
     out = np.empty((len(rows), X.shape[1]))
     for r, i in enumerate(rows):
         lo, hi = S.indptr[i], S.indptr[i + 1]

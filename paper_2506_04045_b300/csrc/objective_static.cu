@@ -24,24 +24,33 @@ using fc::FistaState;
 using fc::FoldArgs;
 using fc::PassArgs;
 
-// Largest number of per-block partial slots a call may use, and the largest
-// padded cluster count (k in {2, 4, 8, 16, 32}).
-constexpr int kMaxParts = 320;
+// The largest padded cluster count (k in {2, 4, 8, 16, 32}); the partial
+// pool holds 320 block partials at that size.
 constexpr int kMaxKP = 32;
+constexpr int kPartsAtMaxKP = 320;
 constexpr int kSumParts = 1024;
 
+// Bytes of one block's partials at padded size KP: a 2 x KP x KP float32 Gram
+// slot and four float64 scalars.
+__host__ __device__ constexpr size_t part_bytes(int KP) { return sizeof(float) * 2 * (size_t)KP * KP + 4 * sizeof(double); }
+
 // Scratch layout (bytes):
-//   [0, G)            Gram partials  kMaxParts * 2 * kMaxKP^2 float32
-//   then              scalar partials kMaxParts * 4 float64
+//   [0, P)            partial pool: parts Gram slots (2 KP^2 float32 each),
+//                     then parts x 4 float64 scalar partials
 //   then              fold result     kMaxKP^2 float64
 //   then              sum-of-squares partials kSumParts float64
 //   then              FistaState
-constexpr size_t kGramBytes = sizeof(float) * (size_t)kMaxParts * 2 * kMaxKP * kMaxKP;
-constexpr size_t kScBytes = sizeof(double) * (size_t)kMaxParts * 4;
+// A smaller k fits more block partials into the same pool (parts_cap).
+constexpr size_t kPoolBytes = part_bytes(kMaxKP) * kPartsAtMaxKP;
 constexpr size_t kABytes = sizeof(double) * (size_t)kMaxKP * kMaxKP;
 constexpr size_t kSumBytes = sizeof(double) * (size_t)kSumParts;
 constexpr size_t kStateBytes = (sizeof(FistaState) + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kGramBytes + kScBytes + kABytes + kSumBytes + kStateBytes;  // about 2.7 MB
+constexpr size_t kScratchBytes = kPoolBytes + kABytes + kSumBytes + kStateBytes;  // about 2.7 MB
+
+// Block partials the pool holds at padded size KP (320 at KP = 32, 1265 at
+// KP = 16, 4837 at KP = 8): a smaller k runs with as many blocks as
+// cluster_objective would.
+constexpr int64_t parts_cap(int KP) { return (int64_t)(kPoolBytes / part_bytes(KP)); }
 
 static __device__ __align__(256) unsigned char g_objective_scratch[kScratchBytes];
 
@@ -76,15 +85,16 @@ cluster_status run_static(const cluster_csr* S, int32_t k, const float* U, cudaS
   FC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fc::fista_pass_kernel<KP, false, true>, L::NT, smem));
   const int64_t n = S->n;
   int64_t parts = (int64_t)sms * (occ < 1 ? 1 : occ);
-  if (parts > kMaxParts) parts = kMaxParts;
+  if (parts > parts_cap(KP)) parts = parts_cap(KP);
   if (parts > (n + L::R - 1) / L::R) parts = (n + L::R - 1) / L::R;
   if (parts < 1) parts = 1;
 
+  // Gram slots first (16-byte aligned rows), the float64 scalars after them
   float* gram_part = reinterpret_cast<float*>(base);
-  double* sc_part = reinterpret_cast<double*>(base + kGramBytes);
-  double* A = reinterpret_cast<double*>(base + kGramBytes + kScBytes);
-  double* sum_part = reinterpret_cast<double*>(base + kGramBytes + kScBytes + kABytes);
-  FistaState* st = reinterpret_cast<FistaState*>(base + kGramBytes + kScBytes + kABytes + kSumBytes);
+  double* sc_part = reinterpret_cast<double*>(base + sizeof(float) * 2 * (size_t)KP * KP * parts);
+  double* A = reinterpret_cast<double*>(base + kPoolBytes);
+  double* sum_part = reinterpret_cast<double*>(base + kPoolBytes + kABytes);
+  FistaState* st = reinterpret_cast<FistaState*>(base + kPoolBytes + kABytes + kSumBytes);
 
   // ||S||_F^2: block partials in scratch, folded on the host in block order
   double hpart[kSumParts];

@@ -3,8 +3,10 @@ advanced together, finished and replaced while others keep running; each
 result equals the same request solved alone."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -62,6 +64,24 @@ def test_served_results_equal_solo_results():
         assert 0 <= times["queue_s"] <= times["total_s"] and times["run_s"] > 0
         iters.add(rep["out_iter"])
     assert len(iters) > 1
+
+
+def test_served_results_match_the_oracle():
+    # a fixed iteration count (stop rule NONE) so that the oracle runs the same
+    # 50 iterations; four requests share the GPU, two are checked in float64
+    picks = [SPECS[2], SPECS[7], SPECS[0], SPECS[4]]      # k = 32 and k = 128 first
+    reqs = [_host(s) for s in picks]
+    srv = pkg.Server(iters_per_tick=8, stop_rule=3, max_iter=50)
+    tickets = [srv.submit(*r) for r in reqs]
+    outs = [srv.wait(t, timeout=300) for t in tickets]
+    srv.close()
+    for spec, (rp, c, v, U0), (U, rep, _) in list(zip(picks, reqs, outs))[:2]:
+        S = sp.csr_matrix((v.astype(np.float64), c, rp), shape=(spec.n, spec.n))
+        o = oracle.fista(S, U0.astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=50, stop="none")
+        assert rep["iters"] == 50 and rep["out_iter"] == 50
+        assert float(np.max(np.abs(U - o.U))) <= 1e-5, spec
+        f_ref = oracle.objective_trace(S, o.U)
+        assert abs(rep["f"] - f_ref) <= 1e-6 * f_ref, (spec, rep["f"], f_ref)
 
 
 def test_budget_limits_residency_and_everything_completes():

@@ -370,6 +370,76 @@ def test_step_rows_reproduces_fista_iterations():
     assert betas[:2] == [0.0, 0.0] and 0 < betas[2] < betas[3] < 1
 
 
+def test_blockwise_share_and_neighbour_only_step():
+    # share = X^T X entry by entry (a double loop over articles) equals the
+    # blockwise sum; one step evaluated from only the sampled articles and their
+    # neighbours, with that share, equals the step from the whole arrays
+    rng = np.random.default_rng(11)
+    X = rng.random((37, 3))
+    brute = np.array([[sum(X[i, a] * X[i, b] for i in range(37)) for b in range(3)] for a in range(3)])
+    blocks = [X[0:5], X[5:6], X[6:30], X[30:37]]
+    assert np.allclose(oracle.gram_blocks(blocks), brute, rtol=1e-14, atol=0)
+    S, U0 = _config1()
+    tau = 1.0 / oracle.lipschitz(S)
+    r = oracle.fista(S, U0, tau, max_iter=4, stop="none", keep_history=True)
+    Xc, Xp = r.history[-1], r.history[-2]
+    beta = oracle.momentum_factors(5)[4]
+    rows = np.array([3, 250, 1999])
+    full = oracle.fista_step_rows(S, Xc, Xp, beta, tau, rows)
+    keep = np.unique(np.concatenate([rows, S[rows].indices]))
+    pos = -np.ones(S.shape[0], dtype=np.int64)
+    pos[keep] = np.arange(keep.size)
+    sub = S[rows].tocoo()
+    local = sp.csr_matrix((sub.data, (pos[rows][sub.row], pos[sub.col])), shape=(keep.size, keep.size))
+    share = oracle.gram_blocks(((Xc[i:i + 300], Xp[i:i + 300]) for i in range(0, S.shape[0], 300)), beta=beta)
+    Y = Xc + beta * (Xc - Xp)
+    assert np.allclose(share, Y.T @ Y, rtol=1e-13, atol=0)
+    part = oracle.fista_step_rows(local, Xc[keep], Xp[keep], beta, tau, pos[rows], share=share)
+    assert np.allclose(part, full, rtol=0, atol=1e-14)
+
+
+def test_fista_momentum_sequence_is_fixed_by_mathematics():
+    # Algorithm 4: t_1 = 1, t_{n+1} = (1 + sqrt(1 + 4 t_n^2)) / 2 and
+    # X^{n+1} = Xbar^n + ((t_n - 1) / t_{n+1}) (Xbar^n - Xbar^{n-1}).  Values
+    # that mathematics fixes independently of any implementation:
+    #   t_2 = (1 + sqrt 5) / 2, the golden ratio (positive root of t^2 = t + 1);
+    #   t_3 = (1 + sqrt(7 + 2 sqrt 5)) / 2, since 1 + 4 t_2^2 = 5 + 4 t_2;
+    #   beta_3 = (t_2 - 1) / t_3 = 0.6180339887 / 2.1935270855 = 0.28175353;
+    #   t_{n+1} is the positive root of t^2 - t = t_n^2, and t_n >= (n + 1) / 2
+    #   (the standard FISTA bound, Beck and Teboulle 2009, by induction).
+    S, U0 = _config1()
+    tau = 1.0 / oracle.lipschitz(S)
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    t3 = (1.0 + math.sqrt(7.0 + 2.0 * math.sqrt(5.0))) / 2.0
+    beta3 = (phi - 1.0) / t3
+    assert abs(beta3 - 0.28175353) < 1e-8
+    r = oracle.fista(S, U0, tau, max_iter=6, stop="none", keep_history=True)
+    ts = r.t_values
+    assert ts[0] == 1.0
+    assert abs(ts[1] - phi) <= 1e-15 and abs(ts[2] - t3) <= 1e-15
+    betas = oracle.momentum_factors(1001)
+    assert betas[0] == 0.0 and betas[1] == 0.0 and abs(betas[2] - beta3) <= 1e-15
+    # the momentum the oracle's iterates carry: Xbar^3 is one step from
+    # X^3 = Xbar^2 + beta_3 (Xbar^2 - Xbar^1); the misreading (t_2 - 1) / t_2 is not
+    hist = [U0] + r.history
+    rows = list(range(0, 2000, 7))
+    right = oracle.fista_step_rows(S, hist[2], hist[1], beta3, tau, rows)
+    wrong = oracle.fista_step_rows(S, hist[2], hist[1], (phi - 1.0) / phi, tau, rows)
+    assert np.max(np.abs(right - hist[3][rows])) <= 1e-13
+    assert np.max(np.abs(wrong - hist[3][rows])) > 1e-9
+    # 1000 iterations on the 7-node example: the quadratic identity and the bound
+    g, _, _ = _toy()
+    U7 = np.full((7, 2), 0.5)
+    U7[0] = (0.9, 0.1)
+    r = oracle.fista(_toy_S(), U7, float(g["step"][0][0]), max_iter=1000, stop="none")
+    ts = np.array(r.t_values)
+    assert ts.size == 1001
+    n = np.arange(1, ts.size + 1)
+    assert np.all(ts >= (n + 1) / 2.0)
+    assert np.allclose(ts[1:] ** 2 - ts[1:], ts[:-1] ** 2, rtol=1e-13, atol=0)
+    assert np.allclose(betas[2:], (ts[1:-1] - 1.0) / ts[2:], rtol=1e-14, atol=0)
+
+
 def test_artificial_two_cluster_recovery():
     # Sect. 5, Experiment 2: from X^0 with ones in the second row, both GPA and
     # FISTA recover the two planted clusters in fewer than 10 iterations.  The

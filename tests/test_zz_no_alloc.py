@@ -6,12 +6,17 @@ where cudaMalloc/cudaFree would synchronise the device).  The allocation-free
 entry point keeps its scratch in a fixed array inside the library; here it is
 checked against the allocating cluster_objective on two calls in a row with
 different inputs (the shared scratch must not carry state from one call into
-the next), and its size limits are checked to fail with EINVAL.  The file is
+the next) for every k it accepts, against the FP64 oracle on a graph with a
+row adjacent to every article, and its size limits are checked to fail with
+EINVAL.  The file is
 named so that pytest collects it last.
 """
+import numpy as np
 import pytest
+import scipy.sparse as sp
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -28,15 +33,35 @@ def _cuda():
     pkg.load()
 
 
-@pytest.mark.parametrize("k", [32, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16, 32])
 def test_static_objective_matches_allocating_entry_point_twice(k):
-    spec = synth.GraphSpec("dcsbm", 30001, k, 90 + k, mean_deg=25.0)
+    spec = synth.GraphSpec("dcsbm", 30001, k, 90 + k, mean_deg=25.0, blocks=max(k, 2))
     rp, c, v = [t.cuda() for t in synth.make_graph(spec)]
     for call in range(2):
         U = synth.dirichlet_u0(spec.n, k, 1000 + 17 * call + k).cuda()
         f_ref = pkg.objective(rp, c, v, U)
         f = pkg.objective_static(rp, c, v, U)
         assert abs(f - f_ref) <= TOL_F * abs(f_ref), (call, f, f_ref)
+
+
+@pytest.mark.parametrize("k", [8, 32])
+def test_static_objective_with_a_hub_row_matches_oracle(k):
+    # the static path splits rows evenly (no chunking of high-degree rows): a
+    # row adjacent to every article lands whole in one block
+    n = 6000
+    rng = np.random.default_rng(5 + k)
+    src = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(0, n, 40000)])
+    dst = np.concatenate([np.arange(1, n, dtype=np.int64), rng.integers(0, n, 40000)])
+    w = (1.0 - rng.random(src.size)).astype(np.float32)
+    rp, c, v = oracle.csr_from_edges(n, src, dst, w)
+    S = sp.csr_matrix((v.astype(np.float64), c, rp), shape=(n, n))
+    g = [torch.from_numpy(x).cuda() for x in (rp, c, v)]
+    for call in range(2):
+        U = synth.dirichlet_u0(n, k, 300 + call)
+        f_ref = oracle.objective_trace(S, U.numpy().astype(np.float64))
+        f = pkg.objective_static(*g, U.cuda())
+        assert abs(f - f_ref) <= TOL_F * f_ref, (call, f, f_ref)
+        assert abs(f - pkg.objective(*g, U.cuda())) <= TOL_F * f_ref
 
 
 def test_static_objective_rejects_what_it_cannot_do_without_memory():
