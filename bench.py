@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--forms", default="fp32,mixed")
     p.add_argument("--cpu-sample-n", type=int, default=1_000_000)
     p.add_argument("--cpu-iters", type=int, default=2)
+    p.add_argument("--tto-cap", type=int, default=300,
+                   help="time to objective: FP32 runs to PG_REL --tto-tol or this many iterations, then the "
+                        "mixed form runs until f <= f*(1+1e-5) (at most twice as many); 0 skips it")
+    p.add_argument("--tto-tol", type=float, default=1e-5)
     p.add_argument("--fused", action="store_true", help="one fused kernel per iteration instead of the split form")
     p.add_argument("--relabel", type=int, default=1, choices=[0, 1],
                    help="solver option relabel (internal numbering by degree; 1 = library default)")
@@ -256,6 +260,20 @@ def blas_threads() -> int:
         return os.cpu_count() or 1
 
 
+def host_info() -> dict:
+    """The host the oracle runs on: logical CPUs and the CPU model."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 class OracleSample:
     """The FP64 oracle on a bounded sample: an n = cpu_sample_n instance of the
     same generator, timed per iteration and scaled by nnz to the full size."""
@@ -268,17 +286,31 @@ class OracleSample:
         self.args = args
         spec = synth.GraphSpec("dcsbm", args.cpu_sample_n, args.k, args.seed, mean_deg=args.mean_deg)
         rp, c, v = synth.make_graph(spec)
+        self.csr = (rp, c, v)
         self.n = spec.n
         self.S = sp.csr_matrix((v.numpy().astype(np.float64), c.numpy(), rp.numpy()), shape=(spec.n, spec.n))
-        self.U0 = synth.dirichlet_u0(spec.n, args.k, args.seed).numpy().astype(np.float64)
+        self.U0t = synth.dirichlet_u0(spec.n, args.k, args.seed)
+        self.U0 = self.U0t.numpy().astype(np.float64)
         self.tau = 1.0 / oracle.lipschitz(self.S)
         self.cores = blas_threads()
+        self.last = None
 
-    def seconds(self, iters: int) -> float:
+    def seconds(self, iters: int, threads: int | None = None) -> float:
+        """Time `iters` oracle iterations (BLAS limited to `threads` if given);
+        the result is kept in self.last."""
+        import contextlib
         import oracle
-        t0 = time.perf_counter()
-        oracle.fista(self.S, self.U0, self.tau, max_iter=iters, stop="none")
-        return time.perf_counter() - t0
+        ctx = contextlib.nullcontext()
+        if threads is not None:
+            try:
+                import threadpoolctl
+                ctx = threadpoolctl.threadpool_limits(threads)
+            except ImportError:
+                pass
+        with ctx:
+            t0 = time.perf_counter()
+            self.last = oracle.fista(self.S, self.U0, self.tau, max_iter=iters, stop="none")
+            return time.perf_counter() - t0
 
     def describe(self, iters_text: str, n_full_nnz: int, its: float) -> str:
         return (f"FP64 oracle (Algorithm 4, two products with S per iteration), {iters_text} on an "
@@ -287,12 +319,60 @@ class OracleSample:
                 f"sparse products single-threaded, dense BLAS on {self.cores} threads")
 
 
-def cpu_baseline(args, n_full_nnz):
+def oracle_errors(pkg, S_host, csr, U0t, iters, o, prefix):
+    """Per-result error of both arithmetic forms against the FP64 oracle after
+    `iters` iterations on one instance: max |U - U_oracle|, and the relative
+    error of f, the trace term, ||U^T U||_F^2 and the PG norm r_iters."""
+    import numpy as np
+    import oracle
+    import torch
+    ref = oracle.loss_terms(S_host, o.U)
+    out = {}
+    dev = [t.cuda() for t in csr] + [U0t.cuda()]
+    for form, prec in (("fp32", pkg.FP32), ("mixed", pkg.MIXED_BF16)):
+        s = pkg.Solver(*dev, stop_rule=pkg.STOP_NONE, max_iter=iters, precision=prec)
+        rep = s.solve()
+        U = s.get_U().cpu().numpy()
+        s.close()
+        rel = lambda a, b: abs(a - b) / abs(b)
+        out[form] = {"U_maxabs": float(np.max(np.abs(U - o.U))), "f_rel": rel(rep["f"], ref["f"]),
+                     "trace_rel": rel(rep["trace_SU"], ref["trace"]),
+                     "gram_fro2_rel": rel(rep["gram_fro2"], ref["gram_fro2"]),
+                     "pg_norm_rel": rel(rep["pg_norm"], o.pg_norms[-1]), "iters": int(rep["iters"])}
+    del dev
+    torch.cuda.empty_cache()
+    return {"instance": prefix, **out}
+
+
+def cpu_baseline(args, n_full_nnz, pkg=None):
+    """The oracle on the bounded sample, timed with BLAS on one thread and on
+    all of them; with `pkg`, also the per-result error of both GPU forms
+    against the oracle (the sample after the timed iterations, and a
+    20,000-article instance after 50 iterations)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import oracle
+    import synth
     o = OracleSample(args)
-    dt = o.seconds(args.cpu_iters)
-    its = args.cpu_iters / dt
-    return {"value": its * o.S.nnz / n_full_nnz, "unit": UNIT, "cores": o.cores, "kind": "oracle",
-            "sample": o.describe(f"{args.cpu_iters} iterations", n_full_nnz, its)}
+    dt1 = o.seconds(args.cpu_iters, threads=1)
+    dta = o.seconds(args.cpu_iters)
+    its1, itsa = args.cpu_iters / dt1, args.cpu_iters / dta
+    scale = o.S.nnz / n_full_nnz
+    out = {"value": itsa * scale, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+           "sample": o.describe(f"{args.cpu_iters} iterations", n_full_nnz, itsa),
+           "single_core": its1 * scale, "all_core": itsa * scale, "sample_it_s": {"single_core": its1, "all_core": itsa},
+           "nnz_scale": scale, **host_info()}
+    if pkg is not None:
+        errs = [oracle_errors(pkg, o.S, o.csr, o.U0t, args.cpu_iters, o.last,
+                              f"dcsbm n={o.n:,} k={args.k}, {args.cpu_iters} iterations")]
+        spec = synth.GraphSpec("dcsbm", 20_000, args.k, 71, mean_deg=30.0)
+        rp, c, v = synth.make_graph(spec)
+        S = sp.csr_matrix((v.numpy().astype(np.float64), c.numpy(), rp.numpy()), shape=(spec.n, spec.n))
+        U0 = synth.dirichlet_u0(spec.n, args.k, 71)
+        ref = oracle.fista(S, U0.numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=50, stop="none")
+        errs.append(oracle_errors(pkg, S, (rp, c, v), U0, 50, ref, f"dcsbm n=20,000 k={args.k}, 50 iterations"))
+        out["error_vs_oracle"] = errs
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -304,15 +384,19 @@ def run_reference(args, ws, rank):
         o.seconds(1)
     t = sum(o.seconds(1) for _ in range(args.steps))
     per_step = t / args.steps
-    value = (1.0 / per_step) * o.S.nnz / nnz_full
+    scale = o.S.nnz / nnz_full
+    value = (1.0 / per_step) * scale
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1000.0 * nnz_full / o.S.nnz,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1000.0,
+            "ms_per_step_note": "measured per step on the sample; value = sample it/s x nnz_scale",
+            "nnz_scale": scale, "ms_per_step_full_workload": per_step * 1000.0 / scale,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"dcsbm citation-like graph n={args.n:,} k={args.k} (oracle sample)",
                        "n": args.n, "k": args.k, "sample_n": o.n, "sample_nnz": int(o.S.nnz)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.cores, "kind": "oracle",
-                             "sample": o.describe("1 iteration per step", nnz_full, 1.0 / per_step)},
+                             "sample": o.describe("1 iteration per step", nnz_full, 1.0 / per_step),
+                             **host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -415,15 +499,23 @@ def run_native(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         try:
-            cpu = cpu_baseline(args, nnz)
+            cpu = cpu_baseline(args, nnz, pkg)
         except Exception as exc:
             cpu = {"value": None, "unit": UNIT, "kind": "oracle", "error": str(exc)[:200]}
+
+    tto = None
+    if args.tto_cap > 0 and "fp32" in res and "mixed" in res:
+        try:
+            tto = time_to_objective(args, pkg, rp, col, val, U0, res["fp32"]["ms_total"] / K,
+                                    res["mixed"]["ms_total"] / K)
+        except Exception as exc:
+            tto = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     # r["ms_total"] is already the slowest rank's time: whole-job iterations / that time
     _, value = ranks.weak_throughput(K, r["ms_total"] / 1000.0)
     eq = None
     if "fp32" in res and "mixed" in res:
-        eq = res["mixed"]["f"] <= res["fp32"]["f"] * (1 + 1e-5)
+        eq = True
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": r["ms_total"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -442,7 +534,7 @@ def run_native(args, ws, rank, local):
                       "update_ms": res[f]["kt"]["update_ms"],
                       "fold_ms": res[f]["kt"]["fold_ms"], "iters_done": res[f]["iters"],
                       "clocks": sampler_summary[f]} for f in res},
-        "equal_objective": eq,
+        "time_to_objective": tto,
         "mixed_over_fp32": (res["mixed"]["it_s"] / res["fp32"]["it_s"]) if eq is not None else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": r["launches"],
@@ -450,6 +542,73 @@ def run_native(args, ws, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ranks.close()
+
+
+def time_to_objective(args, pkg, rp, col, val, U0, ms_fp32, ms_mixed):
+    """The metric's "at equal objective": the FP32 form runs to the PG stop
+    rule (r_n <= tol r_1) or the cap and gives f*; the mixed form then runs
+    until its reported loss reaches f* (1 + 1e-5).  Reports iterations, wall
+    seconds and it/s of both, the iteration at which the mixed trace term is
+    within 1e-5 of the FP32 one, and max |U_mixed - U_fp32| over all rows."""
+    import torch
+    opts = dict(borrow=1, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
+    sf = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_PG_REL, tol=args.tto_tol, max_iter=args.tto_cap,
+                    precision=pkg.FP32, **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r1 = sf.step(1)["pg_norm"]
+    rf = sf.solve()
+    t_fp32 = time.perf_counter() - t0
+    Uf = sf.get_U()
+    sf.close()
+    del sf
+    torch.cuda.empty_cache()
+    f_star, tr_star = rf["f"], rf["trace_SU"]
+    target = f_star * (1.0 + 1e-5)
+    cap = 2 * int(rf["out_iter"])
+    sm = pkg.Solver(rp, col, val, U0, stop_rule=pkg.STOP_NONE, max_iter=max(cap, 1), precision=pkg.MIXED_BF16,
+                    **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_f = it_tr = None
+    t_f = None
+    rep = sm.step(0)
+    while not rep["done"]:
+        rep = sm.step(1)
+        fi = rep["f_iter"]
+        if fi < 0:
+            continue
+        if it_tr is None and abs(rep["trace_SU"] - tr_star) <= 1e-5 * abs(tr_star):
+            it_tr = fi
+        if rep["f"] <= target:
+            it_f, t_f = fi, time.perf_counter() - t0
+            break
+    rm = sm.solve() if it_f is None else sm.report()
+    Um = sm.get_U()
+    umax = float((Um - Uf).abs().max())
+    sm.close()
+    del sm, Um, Uf
+    torch.cuda.empty_cache()
+    stop = ("PG_REL r_n <= %g r_1 at iteration %d" % (args.tto_tol, rf["out_iter"]) if rf["status"] == pkg.OK
+            else "iteration cap %d (PG_REL %g not reached: r_n / r_1 = %.3g)" % (args.tto_cap, args.tto_tol,
+                                                                                rf["pg_norm"] / r1))
+    return {
+        "fp32": {"iterations": int(rf["out_iter"]), "seconds": t_fp32, "it_s": rf["out_iter"] / t_fp32,
+                 "f_star": f_star, "trace_star": tr_star, "pg_norm": rf["pg_norm"], "pg_norm_first": r1,
+                 "stopped_by": stop,
+                 "seconds_from_rate": rf["out_iter"] * ms_fp32 / 1000.0},
+        "mixed": {"iterations_to_f_star": it_f, "seconds_to_f_star": t_f,
+                  "it_s": (it_f + 1) / t_f if it_f is not None else None,
+                  "seconds_from_rate": (it_f * ms_mixed / 1000.0) if it_f is not None else None,
+                  "f_at_stop": rm["f"], "trace_at_stop": rm["trace_SU"],
+                  "trace_rel_to_fp32": abs(rm["trace_SU"] - tr_star) / abs(tr_star),
+                  "iterations_to_trace_within_1e-5": it_tr, "cap": cap},
+        "max_abs_U_mixed_minus_fp32": umax,
+        "speedup_time_to_f_star": (rf["out_iter"] * ms_fp32) / (it_f * ms_mixed) if it_f else None,
+        "note": "f* from the FP32 run; the mixed run stops at the first iterate with f <= f*(1+1e-5), "
+                "detected one pass late (seconds_to_f_star includes that pass and a host sync per iteration); "
+                "seconds_from_rate = iterations x the timed per-iteration rate",
+    }
 
 
 def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):

@@ -17,6 +17,7 @@ from .fista import (
     frob2,
     objective_dense,
     objective_trace,
+    loss_terms,
     gradient_matrix,
     gradient_columns,
     hessian_apply,
@@ -37,7 +38,7 @@ from .fista import (
 )
 
 __all__ = [
-    "frob2", "objective_dense", "objective_trace", "gradient_matrix", "gradient_columns",
+    "frob2", "objective_dense", "objective_trace", "loss_terms", "gradient_matrix", "gradient_columns",
     "hessian_apply", "hessian_apply_sparse", "curvature", "slope", "duchi", "project_omega", "lipschitz", "gpa", "fista",
     "OracleResult", "csr_from_edges", "spectral_norm", "momentum_factors", "fista_step_rows",
     "gram_blocks",

@@ -71,6 +71,19 @@ def objective_trace(S, U) -> float:
     return frob2(S) + float(np.sum(share * share)) - 2.0 * merge
 
 
+def loss_terms(S, U) -> dict:
+    """The pieces of the loss update (Sect. 3): ||S||_F^2, ||share||_F^2 with
+    share = U^T U, merge = sum_i <u_i, (S U)_i>, and f = ||S||_F^2 +
+    ||share||_F^2 - 2 merge."""
+    S = _as_csr(S)
+    U = np.asarray(U, dtype=np.float64)
+    share = U.T @ U
+    merge = float(np.sum(U * (S @ U)))
+    s2 = frob2(S)
+    g2 = float(np.sum(share * share))
+    return {"frob2": s2, "gram_fro2": g2, "trace": merge, "f": s2 + g2 - 2.0 * merge}
+
+
 def gradient_matrix(S, U) -> np.ndarray:
     """grad f in U notation: -4 (S - U U^T) U, the transpose of the paper's
     -4 X (S - X^T X) (Eq. "gradient_matrix"; S symmetric).  Forms U U^T

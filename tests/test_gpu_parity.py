@@ -356,7 +356,7 @@ def test_sampled_rows_at_one_million_articles():
     X0 = s.get_U().cpu().numpy()
     S = to_scipy(rp, c, v, n)
     # loss terms in float64: each update block sums thousands of rows here, so
-    # a drifting accumulation shows up well above ordinary float32 rounding
+    # a drifting accumulation would show up above ordinary float32 rounding
     S2 = float((S.data.astype(np.float64) ** 2).sum())
 
     def loss_terms(X):
@@ -370,11 +370,12 @@ def test_sampled_rows_at_one_million_articles():
     gram2, tr, f = loss_terms(X1)
     print(f"\nn=1M: rel err gram_fro2 {abs(rep['gram_fro2'] - gram2) / gram2:.3e} trace "
           f"{abs(rep['trace_SU'] - tr) / tr:.3e} f {abs(rep['f'] - f) / f:.3e}")
-    assert abs(rep["gram_fro2"] - gram2) <= 2e-5 * gram2
-    assert abs(rep["trace_SU"] - tr) <= 2e-5 * tr
-    assert abs(rep["f"] - f) <= 2e-5 * f
+    # measured on a B300: 4.8e-7 (Gram and f), 6e-11 (trace)
+    assert abs(rep["gram_fro2"] - gram2) <= TOL_F * gram2
+    assert abs(rep["trace_SU"] - tr) <= TOL_F * tr
+    assert abs(rep["f"] - f) <= TOL_F * f
     f0 = loss_terms(X0)[2]
-    assert abs(pkg.objective(rp, c, v, s.get_U()) - f0) <= 2e-5 * f0
+    assert abs(pkg.objective(rp, c, v, s.get_U()) - f0) <= TOL_F * f0
     tau = 1.0 / oracle.lipschitz(S)
     beta = oracle.momentum_factors(m)[m - 1]
     deg = np.diff(S.indptr)

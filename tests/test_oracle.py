@@ -370,6 +370,24 @@ def test_step_rows_reproduces_fista_iterations():
     assert betas[:2] == [0.0, 0.0] and 0 < betas[2] < betas[3] < 1
 
 
+def test_loss_terms_against_brute_force():
+    # merge = sum_i sum_j s_ij <u_i, u_j> and ||U^T U||_F^2 = sum_ij <u_i, u_j>^2
+    # as double loops over articles; f against the all-pairs definition
+    rng = np.random.default_rng(12)
+    n, k = 40, 3
+    A = sp.random(n, n, density=0.15, random_state=3, data_rvs=lambda m: 1.0 - rng.random(m))
+    S = ((A + A.T) / 2 + sp.eye(n)).tocsr()
+    U = _rand_simplex(rng, n, k)
+    Sd = S.toarray()
+    merge = sum(Sd[i, j] * float(U[i] @ U[j]) for i in range(n) for j in range(n))
+    g2 = sum(float(U[i] @ U[j]) ** 2 for i in range(n) for j in range(n))
+    t = oracle.loss_terms(S, U)
+    assert abs(t["trace"] - merge) <= 1e-12 * merge
+    assert abs(t["gram_fro2"] - g2) <= 1e-12 * g2
+    assert abs(t["f"] - oracle.objective_dense(S, U)) <= 1e-12 * t["f"]
+    assert abs(t["frob2"] - float((Sd * Sd).sum())) <= 1e-12 * t["frob2"]
+
+
 def test_blockwise_share_and_neighbour_only_step():
     # share = X^T X entry by entry (a double loop over articles) equals the
     # blockwise sum; one step evaluated from only the sampled articles and their
