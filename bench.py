@@ -46,10 +46,13 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--workload", default="paper", choices=["paper", "batch", "serve", "er2"],
+    p.add_argument("--workload", default="paper", choices=["paper", "batch", "serve", "er2", "rowrate"],
                    help="paper: one n=70M k=32 instance (default); batch: 512 uneven instances; "
                         "serve: Poisson stream of solves through the continuous-batching server; "
-                        "er2: the paper's artificial two-cluster graph (750k nodes, k=2)")
+                        "er2: the paper's artificial two-cluster graph (750k nodes, k=2); "
+                        "rowrate: random-row gather rate (plain loads vs TMA gather4), the product's access pattern")
+    p.add_argument("--table-gb", type=float, default=8.0, help="rowrate: size of the gathered table")
+    p.add_argument("--rows-m", type=int, default=1 << 28, help="rowrate: random rows gathered per launch")
     p.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
     p.add_argument("--drain", type=float, default=30.0, help="serve: seconds to wait for completions afterwards")
@@ -77,9 +80,10 @@ def parse():
                    help="solver option relabel (internal numbering by degree; 1 = library default)")
     p.add_argument("--overlap", type=int, default=0, choices=[0, 1],
                    help="solver option overlap (update of row chunks beside the gather; 0 = library default)")
-    p.add_argument("--update-engine", type=int, default=0, choices=[0, 1],
-                   help="solver option update_engine (0 = tcgen05 for 17 <= k <= 32, library default; "
-                        "1 = warp-level mma.sync); the two give the same bits")
+    p.add_argument("--update-engine", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="solver option update_engine for 17 <= k <= 32 (0 = automatic, library default: "
+                        "streaming from 2^17 articles; 1 = warp-level mma.sync; 2 = tcgen05 per row block; "
+                        "3 = streaming tcgen05 + TMA)")
     return p.parse_args()
 
 
@@ -526,7 +530,8 @@ def run_native(args, ws, rank, local):
                    "l2": "inputs larger than L2 (S 16 GB, iterate 9 GB); no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "iteration_form": "fused" if args.fused else "split",
-                   "update_engine": "warp mma.sync" if args.update_engine else "tcgen05 (TMEM accumulators)",
+                   "update_engine": {0: "automatic (streaming tcgen05 + TMA at this size)", 1: "warp mma.sync",
+                                     2: "tcgen05 per row block", 3: "streaming tcgen05 + TMA"}[args.update_engine],
                    "overlap": "update of 8 row chunks beside the gather" if args.overlap else "gather, then update",
                    "gen_seconds": round(gen_s, 1)},
         "forms": {f: {"it_s": res[f]["it_s"], "ms_per_step": res[f]["ms_total"] / K, "objective": res[f]["f"],
@@ -606,7 +611,8 @@ def time_to_objective(args, pkg, rp, col, val, U0, ms_fp32, ms_mixed):
         "max_abs_U_mixed_minus_fp32": umax,
         "speedup_time_to_f_star": (rf["out_iter"] * ms_fp32) / (it_f * ms_mixed) if it_f else None,
         "note": "f* from the FP32 run; the mixed run stops at the first iterate with f <= f*(1+1e-5), "
-                "detected one pass late (seconds_to_f_star includes that pass and a host sync per iteration); "
+                "detected one pass late (seconds_to_f_star includes that pass and a host sync per iteration; "
+                "the U compared is the mixed run's newest iterate, one pass past it); "
                 "seconds_from_rate = iterations x the timed per-iteration rate",
     }
 
@@ -918,6 +924,67 @@ def run_serve(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_rowrate(args, ws, rank, local):
+    """Random-row gather rate, the access pattern of the product S X isolated:
+    --rows-m uniformly random row indices into a --table-gb table (far larger
+    than L2), rows of 32, 64, 128 and 256 bytes (k = 32 gathers 64-byte bf16
+    rows in the mixed form and 128-byte float32 rows in the FP32 form).  Modes:
+    plain 16-byte loads; the same with the 64-byte L2 fetch hint (rows <= 64 B);
+    TMA tile::gather4 staging through shared memory (64- and 128-byte rows).
+    value = G rows/s of plain loads of 64-byte rows."""
+    import ctypes
+
+    import torch
+    from paper_2506_04045_b300 import build as _b
+    torch.cuda.set_device(local)
+    lib = ctypes.CDLL(_b.build_probe())
+    fn = lib.probe_gather
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    K, W = args.steps, args.warmup
+    nbytes = int(args.table_gb * (1 << 30)) // 256 * 256
+    table = torch.empty(nbytes // 4, dtype=torch.int32, device="cuda").random_()
+    sink = torch.empty(1 << 22, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
+    m = args.rows_m // 4 * 4
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    res = []
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        for rb in (32, 64, 128, 256):
+            rows = nbytes // rb
+            idx = torch.randint(0, rows, (m,), dtype=torch.int32, device="cuda", generator=gen)
+            modes = [0] + ([1] if rb <= 64 else []) + ([2] if rb in (64, 128) else [])
+            for mode in modes:
+                ms = ctypes.c_double(0.0)
+                for reps in (W, K):
+                    rc = fn(table.data_ptr(), rows, rb, idx.data_ptr(), m, mode, 0, max(reps, 1), sink.data_ptr(),
+                            stream.cuda_stream, ctypes.byref(ms))
+                    if rc != 0:
+                        raise RuntimeError(f"probe_gather rows={rb}B mode={mode}: code {rc}")
+                t = ms.value / 1000.0
+                res.append({"row_bytes": rb, "mode": ["plain", "plain+L2::64B", "tma_gather4"][mode],
+                            "ms": ms.value, "G_rows_per_s": m / t / 1e9,
+                            "row_GBps": m * rb / t / 1e9, "with_index_GBps": m * (rb + 4) / t / 1e9,
+                            "frac_of_copy_peak": m * (rb + 4) / t / 1e9 / hbm})
+            del idx
+    head = next(r for r in res if r["row_bytes"] == 64 and r["mode"] == "plain")
+    line = {"metric": "random-row gather rate (G rows/s)", "value": head["G_rows_per_s"], "unit": "G rows/s",
+            "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": head["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{m:,} uniform random rows per launch from a {nbytes / 2**30:.1f} GiB table",
+                       "l2": "table 64x larger than L2; no flush"},
+            "results": res,
+            "roofline": {"bound": "hbm", "achieved": head["with_index_GBps"], "peak": hbm, "unit": "GB/s",
+                         "frac": head["frac_of_copy_peak"], "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "probe_ldg_kernel<64,false>"},
+            "clocks": cs.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -932,6 +999,9 @@ def main():
         return
     if args.workload == "er2":
         run_er2(args, ws, rank, local)
+        return
+    if args.workload == "rowrate":
+        run_rowrate(args, ws, rank, local)
         return
     run_native(args, ws, rank, local)
 

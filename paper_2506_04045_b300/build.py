@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcluster.so")
+PROBE_LIB = os.path.join(HERE, "libgather_probe.so")  # random-row gather probe (bench.py --workload rowrate)
 SOURCES = ["solver.cu", "batch.cu", "server.cu", "objective_static.cu", "csr_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -60,6 +61,20 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, out
     return target
 
 
+def build_probe(force: bool = False) -> str:
+    """Compile the random-row gather probe (its own small library)."""
+    src = os.path.join(CSRC, "probe_gather.cu")
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(src):
+        return PROBE_LIB
+    cmd = [_nvcc(), "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-Xcompiler",
+           "-fvisibility=hidden", *ARCH, src, "-o", PROBE_LIB + ".tmp", "-lcudart"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser()
@@ -69,3 +84,5 @@ if __name__ == "__main__":
     ap.add_argument("-D", dest="defines", action="append", default=[])
     a = ap.parse_args()
     print(build(force=a.force, verbose=True, ptxas_v=a.ptxas_v, out=a.out, defines=tuple(a.defines)))
+    if a.out is None and not a.defines:
+        print(build_probe(force=a.force))

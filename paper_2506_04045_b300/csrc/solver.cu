@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cmath>
 #include <cub/cub.cuh>
+#include <cudaTypedefs.h>
 #include <mutex>
 #include <new>
 #include <string>
@@ -18,6 +19,7 @@
 #include "init_kernels.cuh"
 #include "pass_kernels.cuh"
 #include "tc_update.cuh"
+#include "tc_stream.cuh"
 #include "hessian_kernels.cuh"
 #include "solver_impl.h"
 #include "util.h"
@@ -264,6 +266,63 @@ static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, bo
   FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, tc, s));
 }
 
+// ---- streaming update (tc_stream.cuh) ----
+static cudaError_t stream_setup_attr() {
+  cudaError_t e = cudaFuncSetAttribute(update_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ts::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(update_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts::SMEM);
+}
+
+// Tensor maps of the iterate and product buffers (n x 32 float32): boxes of
+// 32 x 128 rows with 128-byte swizzle; rows at or beyond n read as zero.
+static cluster_status make_stream_maps(cluster_ctx* c) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!encode) {
+    set_error("streaming update: the driver's cuTensorMapEncodeTiled is unavailable");
+    return CLUSTER_ECUDA;
+  }
+  c->smaps = new (std::nothrow) StreamMaps;
+  if (!c->smaps) {
+    set_error("streaming update: host allocation failed");
+    return CLUSTER_ENOMEM;
+  }
+  float* bufs[4] = {c->X[0], c->X[1], c->Z[0], c->Z[1]};
+  CUtensorMap* maps[4] = {&c->smaps->X[0], &c->smaps->X[1], &c->smaps->Z[0], &c->smaps->Z[1]};
+  const cuuint64_t dims[2] = {32, (cuuint64_t)c->n};
+  const cuuint64_t strides[1] = {32 * sizeof(float)};
+  const cuuint32_t box[2] = {32, (cuuint32_t)ts::R};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int i = 0; i < 4; ++i) {
+    const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bufs[i], dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("streaming update: cuTensorMapEncodeTiled failed (%d)", (int)r);
+      return CLUSTER_ECUDA;
+    }
+  }
+  return CLUSTER_OK;
+}
+
+// the row-local update of a split pass with the context's engine
+static void launch_update_ctx(const cluster_ctx* c, const PassArgs& a, cudaStream_t s) {
+  if (c->stream_update) {
+    if (c->mixed) update_stream_kernel<true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+    else update_stream_kernel<false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+  } else {
+    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
+  }
+}
+
 __global__ void set_limit_kernel(FistaState* st, int64_t iters) { st->limit = st->pass + iters; }
 
 // ---------------------------------------------------------------------------
@@ -333,10 +392,14 @@ static void l2_setaside_release() {
 static const int64_t kMinTilesPerBlock = 32;
 // overlapped pass: minimum rows, and update blocks per resident update block
 static const int64_t kOvlMinRows = 1 << 20;
+// update_engine 0 takes the streaming update for solvers of at least this many
+// articles (a persistent grid of one CTA per SM needs a few tiles per CTA)
+static const int64_t kStreamMinRows = 1 << 17;
 static const int kOvlBlockFactor = 4;
 
 void ctx_free(cluster_ctx* c) {
   if (!c) return;
+  delete c->smaps;
   for (cudaGraphExec_t g : c->graph_exec)
     if (g) cudaGraphExecDestroy(g);
   if (c->l2_window_bytes) l2_setaside_release();
@@ -453,7 +516,7 @@ static void enqueue_pass(const cluster_ctx* c, cudaStream_t s, int parity) {
     else
       kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
     if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
-    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
+    launch_update_ctx(c, a, s);
   } else {
     if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
     kp_launch_pass(c->KP, a, c->parts, c->mixed, s);
@@ -699,7 +762,11 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->parts = (int)parts;
   c->heavy_grid = sms * occ;
   c->split = opt.fused_pass == 0;
-  c->tc_update = opt.update_engine == 0;
+  c->tc_update = opt.update_engine != 1;
+  // streaming update for 17 <= k <= 32 on a solo split solver without the
+  // overlapped pass: engine 0 from kStreamMinRows articles, engine 3 always
+  c->stream_update = c->split && capture && c->KP == 32 && !opt.overlap &&
+                     (opt.update_engine == 3 || (opt.update_engine == 0 && n >= kStreamMinRows));
   if (c->split) {
     FC_CUDA(kp_setup_update_attr(c->KP));
     c->spmm_grid = sms * kp_occ_spmm(c->KP, c->mixed);
@@ -712,6 +779,12 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
     pu = std::min<int64_t>(pu, std::max<int64_t>((int64_t)sms, tiles / kMinTilesPerBlock));
     if (pu > tiles) pu = tiles;
     c->parts_upd = (int)std::max<int64_t>(1, pu);
+    if (c->stream_update) {
+      FC_CUDA(stream_setup_attr());
+      const int64_t t128 = (n + fc::ts::R - 1) / fc::ts::R;
+      c->stream_grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, t128));
+      c->parts_upd = 4 * c->stream_grid;  // per CTA: two warpgroups x (high, low) partial slots
+    }
   }
   // rows above H nonzeros are chunked: H is about 64 KB of gathered float32
   // data, and at most an eighth of a resident gather warp's share of the
@@ -730,7 +803,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   // contexts use kOvlBlockFactor times more (smaller) update blocks, with or
   // without the overlap, so that both schedules sum the same partials (same
   // bits) and the last chunk's update is short.
-  if (c->split && c->relabeled && n >= kOvlMinRows) {
+  if (c->split && c->relabeled && n >= kOvlMinRows && !c->stream_update) {
     int* dflag = nullptr;
     int hflag = 1;
     FC_CUDA(cudaMalloc(&dflag, sizeof(int)));
@@ -793,6 +866,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * slots));
   FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * slots));
   FC_CUDA(cudaMalloc(&c->st, sizeof(FistaState)));
+  if (c->stream_update) FC_TRY(make_stream_maps(c));
 
   // Xbar^0 = U0 in buffer 0; buffer 1 starts as a copy (momentum is 0 for the first two passes)
   if (c->relabeled)
@@ -1044,7 +1118,7 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
       cudaEventRecord(e[1], s);
       if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
       cudaEventRecord(e[2], s);
-      kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
+      launch_update_ctx(c, a, s);
     } else {
       if (c->n_chunks > 0) kp_launch_heavy(c->KP, a, c->heavy_grid, c->mixed, false, s);
       cudaEventRecord(e[1], s);

@@ -10,6 +10,10 @@
 #include "pass_kernels.cuh"
 #include "state.h"
 
+namespace fc {
+struct StreamMaps;
+}
+
 struct cluster_ctx {
   int dev = 0;
   cudaStream_t stream = nullptr;      // caller's stream
@@ -52,6 +56,11 @@ struct cluster_ctx {
   bool split = true;
   int parts_upd = 1;                    // blocks (and partial slots) of the update kernel
   bool tc_update = true;                // update on tcgen05 where the kernel exists (k <= 32)
+  // streaming update (tc_stream.cuh, KP = 32): one CTA per SM over 128-row
+  // tiles loaded by TMA through these tensor maps of X[0..1], Z[0..1]
+  bool stream_update = false;
+  int stream_grid = 0;
+  fc::StreamMaps* smaps = nullptr;
   int spmm_grid = 1;
   // overlapped pass (opt.overlap): row chunk c's update runs on side_stream
   // once the gather units that cover its rows (ovl_units[c+1]) are done, while

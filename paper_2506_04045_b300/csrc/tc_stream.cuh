@@ -1,0 +1,594 @@
+// Streaming row-local update of the split iteration for KP = 32 (17 <= k <=
+// 32) on sm_103a: one thread per row, tiles of 128 rows moved by TMA, both
+// dense contractions on the fifth-generation tensor cores.
+//
+// Same mathematics as update_kernel / update_tc_kernel, per row i:
+//   y_i  = xbar^{n-1}_i + beta (xbar^{n-1}_i - xbar^{n-2}_i)          (X^n, Alg. 4)
+//   SY_i = z_i + beta (z_i - z^{prev}_i)                             (S X^n by linearity)
+//   xbar^n_i = P_simplex(y_i + 4 tau (SY_i - y_i G(Y)))              (Eq. "gradient_column", Alg. 1)
+// with the trace term <xbar^{n-1}_i, z_i> of the loss update (Sect. 3), the
+// projected-gradient norm ||y_i - xbar^n_i||^2 and the Gram partials of
+// Xbar^n and of Y^{n+1} = Xbar^n + beta_{n+1} (Xbar^n - Xbar^{n-1}).
+//
+// Layout and roles (one CTA per SM, persistent over a contiguous range of
+// tiles; 288 threads):
+//   * two compute warpgroups (warps 0-3 and 4-7) take the CTA's tiles in turn;
+//     thread t of a warpgroup owns row t of its tile and keeps the row's 32
+//     features in registers, so the projection, the trace term and the norm
+//     are sums inside one thread (no shuffles);
+//   * one helper thread (warp 8) issues the TMA loads of the four input tiles
+//     (z, xbar^{n-1}, xbar^{n-2}, z^{prev}: 4 x 16 KB, 128-byte swizzle, which
+//     makes every thread's 16-byte reads of its own row conflict-free) and all
+//     tcgen05.mma instructions, polling the warpgroups' mbarriers.
+//   * y G(Y): kind::tf32, 3xTF32 (hi/lo split), M = 128 = the tile's rows, so
+//     row r of the accumulator is TMEM lane r and each thread reads its own
+//     row back (tcgen05.ld 32x32b).  The y operand (hi, lo) goes to the
+//     Gram operand's area (free again once the previous tile's Gram has
+//     completed), so the whole input stage is free as soon as the warpgroup
+//     has read its rows: the next tile's loads overlap y G and the projection.
+//   * Gram of [Xbar^n | Y^{n+1}] (64 features): kind::f16 with both operands
+//     MN-major, i.e. the row-major tile itself (no transpose).  Each value is
+//     scaled by 2^13 and split into two float16 parts h + l (h = f16(s x),
+//     l = f16(s x - h)); h h + h l + l h carries the product to about 2^-22
+//     relative, like 3xTF32, and values below the float16 normal range lose
+//     only an absolute 2^-38 after the scale.  The accumulator is read back
+//     per tile and added into float pairs (TwoSum) in the threads, so the
+//     partial of a CTA does not drift over thousands of tiles; the h h
+//     products of the tile's two row halves go to two accumulators, which
+//     halves the bias of the tensor core's truncating accumulation.
+//
+// Every wait is bounded (polls of bounded length, about one second in all);
+// a warpgroup whose wait gives up raises an abort flag that ends every role's
+// loop, the helper waits (bounded) for its loads and MMAs still in flight, and
+// the fold ends the run with CLUSTER_ETIMEOUT.  Test hook bit 0 withholds the
+// commit of y G, which drives that path without any fault.
+#pragma once
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "tc_update.cuh"
+
+namespace fc {
+
+// Tensor maps of the four n x 32 float32 buffers the streaming update reads
+// (box 32 x 128 rows, 128-byte swizzle, rows beyond n read as zero).
+struct StreamMaps {
+  CUtensorMap X[2];
+  CUtensorMap Z[2];
+};
+
+namespace ts {
+
+constexpr int R = 128;                  // rows per tile
+constexpr int NT = 288;                 // 2 x 128 compute threads + one helper warp
+constexpr int TILE_B = R * 128;         // one tile of one input: 16 KB
+constexpr int STAGE_B = 4 * TILE_B;     // z, xbar^{n-1}, xbar^{n-2}, z^{prev}
+constexpr int GOP_B = 2 * R * 128;      // Gram operand: h and l, 128 rows x 64 float16
+constexpr int OFF_GH = 0, OFF_GL = 4096, OFF_WG = 8192;
+constexpr int WG_B = STAGE_B + GOP_B;   // 96 KB per warpgroup
+constexpr size_t SMEM = (size_t)OFF_WG + 2 * (size_t)WG_B + 1024;  // + alignment slack
+constexpr int TMEM_COLS = 512;
+// TMEM columns per warpgroup w (base 256 w): y G (32), Gram accumulators A, B
+// (64 each), 32 columns in which each thread keeps its 16 float pairs of the
+// running Gram partial, and 32 that hold its row of xbar^{n-1} between the
+// loads and the Gram operand (its own lane; registers are the scarce resource)
+constexpr int COL_YG = 0, COL_GA = 64, COL_GB = 128, COL_ACC = 192, COL_PV = 224, COL_WG = 256;
+constexpr float kScale = 8192.0f;                          // 2^13
+constexpr float kUnscale2 = 1.0f / (8192.0f * 8192.0f);   // 2^-26, exact
+// mbarriers of warpgroup w: w * 5 + {full, yready, ygdone, gready, grdone}; [10] final commit
+constexpr int BAR_FULL = 0, BAR_YREADY = 1, BAR_YGDONE = 2, BAR_GREADY = 3, BAR_GRDONE = 4, NBARS = 11;
+// the helper gives up after this many idle rounds of at least kIdleNs (about one second)
+constexpr uint32_t kIdleRounds = 1u << 24, kIdleNs = 64u;
+
+static_assert(SMEM <= 232448, "shared memory of the streaming update");
+
+__host__ __device__ constexpr uint32_t idesc_tf32_m128() { return tc::idesc_tf32(128, 32); }
+// kind::f16: float32 accumulator (bits 4-5 = 1), A and B float16 (bits 7-9,
+// 10-12 = 0), both MN-major (bits 15, 16), N / 8 at bit 17, M / 16 at bit 24
+__host__ __device__ constexpr uint32_t idesc_f16_mn(int M, int N) {
+  return (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// MN-major operand with 128-byte swizzle whose MN extent is one 128-byte atom
+// (64 float16): groups of 8 K-rows 1024 bytes apart.  The byte offset between
+// atoms along MN is not used at this width; it is set to the same 1024.
+__device__ __forceinline__ uint64_t desc_mn128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(1024 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_init_n(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// non-blocking: true if the phase with this parity has completed
+__device__ __forceinline__ bool test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 2-D tiled TMA load of the box at (x, y) into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// TMEM lane of the calling thread (32 lanes of its warp's quarter), 32
+// consecutive columns from taddr into v
+__device__ __forceinline__ void ld32x32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+// the inverse: 32 consecutive columns of the calling thread's lane from v
+__device__ __forceinline__ void st32x32(uint32_t taddr, const float* v) {
+  uint32_t r[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(v[j]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Shared state of one CTA of the streaming update.
+struct StreamCta {
+  uint8_t* sm;       // 1024-aligned dynamic shared memory
+  uint32_t sb;       // its shared-window address
+  uint32_t tmem;     // TMEM base (512 columns)
+  uint32_t bars;     // shared address of the NBARS mbarriers (8 bytes each)
+  int* flags;        // [0] abort (a wait gave up), [1] test hooks
+  int64_t t0;        // first tile of this CTA
+  int cnt;           // tiles of this CTA (warpgroup w takes local tiles w, w + 2, ...)
+  __device__ __forceinline__ uint32_t bar(int w, int i) const { return bars + 8u * (uint32_t)(w * 5 + i); }
+  __device__ __forceinline__ bool aborted() const { return *reinterpret_cast<volatile int*>(flags) != 0; }
+};
+
+// The helper thread: TMA loads into a warpgroup's stage once the warpgroup
+// has read its previous tile's rows (its y-ready arrival), y G once the
+// warpgroup has written its y operand, the Gram once it has written the Gram
+// operand.  The three chains of both warpgroups are polled in turn, so
+// neither warpgroup waits for the other.  Returns after every issued load
+// has landed and every issued MMA has completed (each bounded).
+__device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMaps& m, int64_t pass) {
+  const CUtensorMap* mz = &m.Z[(pass + 1) & 1];   // S Xbar^{pass}
+  const CUtensorMap* mp = &m.X[pass & 1];         // Xbar^{pass}
+  const CUtensorMap* mq = &m.X[(pass + 1) & 1];   // Xbar^{pass-1}
+  const CUtensorMap* mzp = &m.Z[pass & 1];        // S Xbar^{pass-1}
+  prefetch_map(mz);
+  prefetch_map(mp);
+  prefetch_map(mq);
+  prefetch_map(mzp);
+  const bool hook = (c.flags[1] & 1) != 0;
+  const int ntw[2] = {(c.cnt + 1) / 2, c.cnt / 2};
+  int nl[2] = {0, 0}, ny[2] = {0, 0}, ng[2] = {0, 0};
+  uint32_t idle = 0;
+  for (;;) {
+    bool all = true, prog = false;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if (ng[w] < ntw[w]) all = false;
+      const uint32_t st = c.sb + OFF_WG + (uint32_t)w * WG_B;
+      // load the warpgroup's next tile once the stage is free
+      if (nl[w] < ntw[w] && (nl[w] == 0 || test_wait(c.bar(w, BAR_YREADY), (uint32_t)(nl[w] - 1) & 1u))) {
+        const int row = (int)((c.t0 + 2 * nl[w] + w) * R);
+        const uint32_t full = c.bar(w, BAR_FULL);
+        expect_tx(full, STAGE_B);
+        tma_load_2d(st + 0 * TILE_B, mz, 0, row, full);
+        tma_load_2d(st + 1 * TILE_B, mp, 0, row, full);
+        tma_load_2d(st + 2 * TILE_B, mq, 0, row, full);
+        tma_load_2d(st + 3 * TILE_B, mzp, 0, row, full);
+        ++nl[w];
+        prog = true;
+      }
+      // y G(Y): A = y hi / lo (in the Gram operand's area), B = G(Y) hi / lo
+      if (ny[w] < nl[w] && test_wait(c.bar(w, BAR_YREADY), (uint32_t)ny[w] & 1u)) {
+        tc::fence_after_sync();
+        const uint32_t d = c.tmem + (uint32_t)(w * COL_WG + COL_YG);
+        const uint32_t ya = st + STAGE_B;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ah = tc::desc_k128(ya + 32 * ks), al = tc::desc_k128(ya + TILE_B + 32 * ks);
+          const uint64_t bh = tc::desc_k128(c.sb + OFF_GH + 32 * ks), bl = tc::desc_k128(c.sb + OFF_GL + 32 * ks);
+          tc::mma(d, al, bh, idesc_tf32_m128(), ks > 0);
+          tc::mma(d, ah, bl, idesc_tf32_m128(), 1);
+          tc::mma(d, ah, bh, idesc_tf32_m128(), 1);
+        }
+        if (!hook) tc::commit(c.bar(w, BAR_YGDONE));
+        ++ny[w];
+        prog = true;
+      }
+      // Gram of [Xbar^n | Y^{n+1}] over the tile's rows (K = 128, 8 steps of 16)
+      if (ng[w] < ny[w] && test_wait(c.bar(w, BAR_GREADY), (uint32_t)ng[w] & 1u)) {
+        tc::fence_after_sync();
+        const uint32_t da = c.tmem + (uint32_t)(w * COL_WG + COL_GA), db = c.tmem + (uint32_t)(w * COL_WG + COL_GB);
+        const uint32_t g = st + STAGE_B;
+        constexpr uint32_t ID = idesc_f16_mn(64, 64);
+        // the small cross products first, then h h: rows 0-63 into A, 64-127 into B
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint64_t h = desc_mn128(g + 2048 * ks), l = desc_mn128(g + TILE_B + 2048 * ks);
+          mma_f16(da, l, h, ID, ks > 0);
+          mma_f16(da, h, l, ID, 1);
+        }
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint64_t h = desc_mn128(g + 2048 * ks);
+          if (ks < 4) mma_f16(da, h, h, ID, 1);
+          else mma_f16(db, h, h, ID, ks > 4);
+        }
+        tc::commit(c.bar(w, BAR_GRDONE));
+        ++ng[w];
+        prog = true;
+      }
+    }
+    if (all) break;
+    if (prog) {
+      idle = 0;
+    } else {
+      if (c.aborted() || ++idle > kIdleRounds) {
+        *reinterpret_cast<volatile int*>(c.flags) = 1;
+        break;
+      }
+      __nanosleep(kIdleNs);
+    }
+  }
+  // nothing of this thread may be in flight when the CTA exits
+  const uint32_t fin = c.bars + 8u * 10u;
+  tc::commit(fin);
+  tc::bar_wait(fin, 0);
+  for (int w = 0; w < 2; ++w)
+    if (nl[w] > 0) tc::bar_wait(c.bar(w, BAR_FULL), (uint32_t)(nl[w] - 1) & 1u);
+}
+
+// One compute thread: row t of each tile of warpgroup w.  Per tile: the four
+// input rows from the stage (conflict-free swizzled reads), the trace term,
+// y and SY; the y operand over the rows just read; y G back from TMEM; step
+// and projection onto the simplex inside the thread (Michelot's active-set
+// iteration, the same threshold as Algorithm 1); the new row and its bfloat16
+// copy to global memory; the Gram operand of [Xbar^n | Y^{n+1}].  Partial
+// results go to slots slot0 + 2 w (the float pairs' high parts and the
+// scalars) and slot0 + 2 w + 1 (the low parts).
+template <bool MIXED>
+__device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCta& c, int64_t pass, int slot0,
+                                               double (*red)[4]) {
+  const int tid = threadIdx.x, w = tid >> 7, t = tid & 127, qw = (tid >> 5) & 3, lane = tid & 31;
+  const FistaState* st = a.st;
+  const float beta = (float)st->beta, beta_next = (float)st->beta_next;
+  const float tau4 = (float)(4.0 * st->tau);
+  float* Qx = (pass & 1) ? a.X0 : a.X1;              // Xbar^{pass+1} out (over Xbar^{pass-1})
+  __nv_bfloat16* XSo = (pass & 1) ? a.XS0 : a.XS1;
+  const int k = a.k;
+  uint8_t* stp = c.sm + OFF_WG + w * WG_B;
+  uint8_t* gp = stp + STAGE_B;
+  // this warp's TMEM lane quarter, this warpgroup's columns
+  const uint32_t tw = c.tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(w * COL_WG);
+  const int gm = qw >> 1;  // Gram rows of this warp's quarter: matrix 0 (Xbar^n) or 1 (Y^{n+1})
+  {
+    float z[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = 0.f;
+    st32x32(tw + COL_ACC, z);  // running Gram partial: [0, 16) high parts, [16, 32) low parts
+  }
+  float tr_hi = 0.f, tr_lo = 0.f, pg_hi = 0.f, pg_lo = 0.f;
+  int bad = 0;
+  bool dead = false;
+  const int ntw = (c.cnt + 1 - w) / 2;
+  const int swz = t & 7;
+
+  // bounded wait, the same outcome on every lane of the warp
+  auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+    bool ok = false;
+    for (uint32_t i = 0; i < tc::kWaitPolls && !ok; ++i) {
+      ok = tc::bar_try(bar, par);
+      if (!ok && c.aborted()) break;
+    }
+    ok = __all_sync(kFull, ok);
+    if (!ok) {
+      dead = true;
+      *reinterpret_cast<volatile int*>(c.flags) = 1;
+    }
+    tc::fence_after_sync();
+    return ok;
+  };
+  // the previous tile's Gram (both accumulators) into the float pairs
+  auto gram_back = [&]() {
+    float g[32];
+    ld32x32(tw + COL_ACC, g);
+#pragma unroll
+    for (int acc = 0; acc < 2; ++acc) {
+#pragma unroll
+      for (int cg = 0; cg < 2; ++cg) {
+        float v[8];
+        tc::ld16x16(tw + (acc ? COL_GB : COL_GA) + 32 * gm + 16 * cg, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) two_sum_acc(g[8 * cg + j], g[16 + 8 * cg + j], v[j]);
+      }
+    }
+    st32x32(tw + COL_ACC, g);
+  };
+
+  for (int jj = 0; jj < ntw; ++jj) {
+    const int64_t row = (c.t0 + 2 * jj + w) * R + t;
+    const bool active = row < a.n;
+    if (!wait(c.bar(w, BAR_FULL), (uint32_t)jj & 1u)) break;
+    // the Gram operand's area takes this tile's y operand once the previous
+    // tile's Gram has completed
+    if (jj > 0) {
+      if (!wait(c.bar(w, BAR_GRDONE), (uint32_t)(jj - 1) & 1u)) break;
+      gram_back();
+    }
+    float y[32], sy[32], pv[32];
+    float d = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const int off = t * 128 + ((ch ^ swz) << 4);
+      const float4 z4 = *reinterpret_cast<const float4*>(stp + 0 * TILE_B + off);
+      const float4 p4 = *reinterpret_cast<const float4*>(stp + 1 * TILE_B + off);
+      const float4 q4 = *reinterpret_cast<const float4*>(stp + 2 * TILE_B + off);
+      const float4 r4 = *reinterpret_cast<const float4*>(stp + 3 * TILE_B + off);
+      const float zv[4] = {z4.x, z4.y, z4.z, z4.w}, pvv[4] = {p4.x, p4.y, p4.z, p4.w};
+      const float qv[4] = {q4.x, q4.y, q4.z, q4.w}, zp[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int f = 4 * ch + q;
+        pv[f] = pvv[q];
+        d = fmaf(pvv[q], zv[q], d);
+        y[f] = fmaf(beta, pvv[q] - qv[q], pvv[q]);
+        sy[f] = fmaf(beta, zv[q] - zp[q], zv[q]);
+      }
+      // y operand (row t, 128-byte swizzle, K-major): hi, lo
+      split_store4(reinterpret_cast<float*>(gp + off), reinterpret_cast<float*>(gp + TILE_B + off), &y[4 * ch]);
+    }
+    st32x32(tw + COL_PV, pv);
+    if (!isfinite(d)) bad = 1;  // d is finite exactly when every z of the row is
+    if (active) two_sum_acc(tr_hi, tr_lo, d);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    arrive(c.bar(w, BAR_YREADY));
+    if (!wait(c.bar(w, BAR_YGDONE), (uint32_t)jj & 1u)) break;
+
+    float v[32];
+    ld32x32(tw + COL_YG, v);  // (y G(Y))_i of this row
+    float s = 0.f;
+#pragma unroll
+    for (int f = 0; f < 32; ++f) {
+      v[f] = fmaf(tau4, sy[f] - v[f], y[f]);
+      s += v[f];  // padded features are exactly zero
+    }
+#pragma unroll
+    for (int f = 0; f < 32; ++f)
+      if (f >= k) v[f] = -INFINITY;
+    // Michelot: theta = (sum over A of v - 1) / |A|, A = {v > theta}, until |A| is stable
+    float cnt = (float)k;
+    float theta = __fdividef(s - 1.0f, cnt);
+    for (int it = 0; it <= 32; ++it) {
+      float s2 = 0.f, c2 = 0.f;
+#pragma unroll
+      for (int f = 0; f < 32; ++f) {
+        const bool on = v[f] > theta;
+        s2 += on ? v[f] : 0.f;
+        c2 += on ? 1.f : 0.f;
+      }
+      if (c2 == cnt) break;
+      cnt = c2;
+      theta = __fdividef(s2 - 1.0f, cnt);
+    }
+    float pg = 0.f;
+#pragma unroll
+    for (int f = 0; f < 32; ++f) {
+      v[f] = fmaxf(v[f] - theta, 0.0f);  // xbar^n_i
+      const float dd = y[f] - v[f];
+      pg = fmaf(dd, dd, pg);
+    }
+    if (!isfinite(pg)) bad = 1;
+    if (active) {
+      two_sum_acc(pg_hi, pg_lo, pg);
+      float4* xo = reinterpret_cast<float4*>(Qx + row * 32);
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) xo[ch] = make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
+      if constexpr (MIXED) {
+        uint4* bo = reinterpret_cast<uint4*>(XSo + row * 32);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t u[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * ch + 2 * e], v[8 * ch + 2 * e + 1]);
+            u[e] = *reinterpret_cast<const uint32_t*>(&b2);
+          }
+          bo[ch] = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+      }
+    }
+    // the y operand has been read (y G completed): s [xbar^n | y^{n+1}] as
+    // float16 h + l over it, row t, chunk ch = features 8 ch ..
+    ld32x32(tw + COL_PV, pv);
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      uint32_t hu[4], lu[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float val[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int f = 8 * (ch & 3) + 2 * e + h;
+          const float xv = v[f];
+          const float g = ch < 4 ? xv : fmaf(beta_next, xv - pv[f], xv);
+          val[h] = active ? g * kScale : 0.f;
+        }
+        const __half2 hh = __floats2half2_rn(val[0], val[1]);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(val[0] - hf.x, val[1] - hf.y);
+        hu[e] = *reinterpret_cast<const uint32_t*>(&hh);
+        lu[e] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+      const int off = t * 128 + ((ch ^ swz) << 4);
+      *reinterpret_cast<uint4*>(gp + off) = make_uint4(hu[0], hu[1], hu[2], hu[3]);
+      *reinterpret_cast<uint4*>(gp + TILE_B + off) = make_uint4(lu[0], lu[1], lu[2], lu[3]);
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    arrive(c.bar(w, BAR_GREADY));
+  }
+  if (!dead && ntw > 0 && wait(c.bar(w, BAR_GRDONE), (uint32_t)(ntw - 1) & 1u)) gram_back();
+
+  // ---- partial results (fixed order: bit-reproducible) ----
+  double trd = (double)tr_hi + (double)tr_lo, pgd = (double)pg_hi + (double)pg_lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    trd += __shfl_down_sync(kFull, trd, o);
+    pgd += __shfl_down_sync(kFull, pgd, o);
+  }
+  bad = __reduce_or_sync(kFull, bad);
+  if (lane == 0) {
+    red[4 * w + qw][0] = trd;
+    red[4 * w + qw][1] = pgd;
+    red[4 * w + qw][2] = (double)bad;
+    red[4 * w + qw][3] = dead ? 1.0 : 0.0;
+  }
+  named_sync(1 + w, 128);
+  const int shi = slot0 + 2 * w, slo = shi + 1;
+  if (t == 0) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < 4; ++q) acc[q] += red[4 * w + i][q];
+    for (int q = 0; q < 4; ++q) {
+      a.sc_part[shi * 4 + q] = acc[q];
+      a.sc_part[slo * 4 + q] = 0.0;
+    }
+  }
+  constexpr int E2 = 32 * 32;
+  const int r = 16 * (qw & 1) + (lane & 15);
+  float g[32];
+  ld32x32(tw + COL_ACC, g);
+#pragma unroll
+  for (int cg = 0; cg < 2; ++cg) {
+    const size_t o = (size_t)gm * E2 + (size_t)r * 32 + 16 * cg + 8 * (lane >> 4);
+    float* hi = a.gram_part + (size_t)shi * 2 * E2 + o;
+    float* lo = a.gram_part + (size_t)slo * 2 * E2 + o;
+    const float* H = g + 8 * cg;
+    const float* Lw = g + 16 + 8 * cg;
+    reinterpret_cast<float4*>(hi)[0] = make_float4(H[0] * kUnscale2, H[1] * kUnscale2, H[2] * kUnscale2, H[3] * kUnscale2);
+    reinterpret_cast<float4*>(hi)[1] = make_float4(H[4] * kUnscale2, H[5] * kUnscale2, H[6] * kUnscale2, H[7] * kUnscale2);
+    reinterpret_cast<float4*>(lo)[0] =
+        make_float4(Lw[0] * kUnscale2, Lw[1] * kUnscale2, Lw[2] * kUnscale2, Lw[3] * kUnscale2);
+    reinterpret_cast<float4*>(lo)[1] =
+        make_float4(Lw[4] * kUnscale2, Lw[5] * kUnscale2, Lw[6] * kUnscale2, Lw[7] * kUnscale2);
+  }
+}
+
+}  // namespace ts
+
+// Split iteration, step 3, streaming form for KP = 32: CTA b takes tiles
+// [b T / G, (b+1) T / G) of the T = ceil(n / 128) row tiles and partial slots
+// 4 b .. 4 b + 3 (warpgroup w: 4 b + 2 w high parts and scalars, 4 b + 2 w + 1
+// low parts).  Launch with ts::NT threads, ts::SMEM bytes of dynamic shared
+// memory and at most one CTA per SM (it allocates all 512 TMEM columns).
+template <bool MIXED>
+__global__ void __launch_bounds__(ts::NT, 1) update_stream_kernel(PassArgs a, const __grid_constant__ StreamMaps maps) {
+  using namespace ts;
+  volatile FistaState* vs = a.st;
+  if (vs->done || vs->pass >= vs->limit) return;
+  const int64_t pass = vs->pass;
+  extern __shared__ __align__(1024) uint8_t ts_smem_raw[];
+  __shared__ __align__(8) uint64_t bars[NBARS];
+  __shared__ uint32_t tslot;
+  __shared__ int flags[2];
+  __shared__ double red[8][4];
+  StreamCta c;
+  c.sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ts_smem_raw) + 1023) & ~(uintptr_t)1023);
+  c.sb = tc::saddr(c.sm);
+  c.bars = tc::saddr(bars);
+  c.flags = flags;
+  const int64_t T = (a.n + R - 1) / R;
+  c.t0 = T * (int64_t)blockIdx.x / gridDim.x;
+  c.cnt = (int)(T * (int64_t)(blockIdx.x + 1) / gridDim.x - c.t0);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(&tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int w = 0; w < 2; ++w) {
+      bar_init_n(c.bar(w, BAR_FULL), 1);
+      bar_init_n(c.bar(w, BAR_YREADY), 128);
+      bar_init_n(c.bar(w, BAR_YGDONE), 1);
+      bar_init_n(c.bar(w, BAR_GREADY), 128);
+      bar_init_n(c.bar(w, BAR_GRDONE), 1);
+    }
+    bar_init_n(c.bars + 8u * 10u, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    flags[0] = 0;
+    flags[1] = vs->hooks;
+  }
+  // G(Y) (symmetric: its rows serve as the K-major B operand of y G), hi / lo
+  if (tid < 256) {
+    const int n = tid >> 3, ch = tid & 7;
+    float g[4];
+    load_row<4>(a.Gy + n * 32 + 4 * ch, g);
+    split_store4(reinterpret_cast<float*>(c.sm + OFF_GH + tc::sw_chunk(n, ch)),
+                 reinterpret_cast<float*>(c.sm + OFF_GL + tc::sw_chunk(n, ch)), g);
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  c.tmem = tslot;
+  if (warp < 8) {
+    stream_compute<MIXED>(a, c, pass, 4 * (int)blockIdx.x, red);
+  } else {
+    if ((tid & 31) == 0) stream_helper(c, maps, pass);
+    __syncwarp();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace fc
