@@ -29,7 +29,10 @@ struct BatchClass {
   // device copies of the per-instance tables
   PassArgs* d_args = nullptr;
   FoldArgs* d_folds = nullptr;
-  int64_t* d_unit_base = nullptr;
+  int64_t* d_unit_base = nullptr;   // gather unit prefix sums of the current shape (one of d_ub)
+  int64_t* d_ub[kGatherShapes] = {};  // per gather tile shape (rows per unit differ)
+  int64_t units_s[kGatherShapes] = {};
+  int shape = 0;                      // gather tile shape (BShape index)
   int64_t* d_heavy_base = nullptr;
   int32_t* d_item_inst = nullptr;
   int32_t* d_item_slot = nullptr;
@@ -83,24 +86,47 @@ struct BOps {
     const int64_t fin_threads = bc.heavy * L::T;
     bc.fin_grid = (int)std::max<int64_t>(1, std::min<int64_t>((fin_threads + 255) / 256, 4096));
   }
+  // the gather of shape `shape` (its own unit table)
+  template <int S>
+  static void spmm_s(const BatchClass& bc, int grid, cudaStream_t s) {
+    BatchMeta m = bc.meta;
+    m.unit_base = bc.d_ub[S];
+    if (bc.mixed) batch_spmm_kernel<KP, true, S><<<grid, L::NT, 0, s>>>(m);
+    else batch_spmm_kernel<KP, false, S><<<grid, L::NT, 0, s>>>(m);
+  }
+  static void spmm(const BatchClass& bc, int shape, int grid, cudaStream_t s) {
+    static_assert(kGatherShapes == 3, "gather shapes");
+    if (shape == 1) spmm_s<1>(bc, grid, s);
+    else if (shape == 2) spmm_s<2>(bc, grid, s);
+    else spmm_s<0>(bc, grid, s);
+  }
   static void iteration(const BatchClass& bc, cudaStream_t s) {
     cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
-    if (bc.mixed) batch_spmm_kernel<KP, true><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
-    else batch_spmm_kernel<KP, false><<<bc.spmm_grid, L::NT, 0, s>>>(bc.meta);
+    spmm(bc, bc.shape, bc.spmm_grid, s);
     if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
     upd_fn(bc.mixed, bc.tc)<<<bc.upd_grid, L::NT, upd_smem(bc.tc), s>>>(bc.meta);
     batch_fold_kernel<KP><<<(int)bc.members.size() * fold_blocks<KP>(false), 256, 0, s>>>(bc.meta);
   }
-  static int64_t units(const cluster_ctx* c) {
-    return c->mixed ? spmm_units<KP, true>(c->n, c->n_heavy, c->n_chunks)
-                    : spmm_units<KP, false>(c->n, c->n_heavy, c->n_chunks);
+  template <int S>
+  static int64_t units_s(const cluster_ctx* c) {
+    constexpr int R1 = BShape<KP, true, S>::RPU, R0 = BShape<KP, false, S>::RPU;
+    return c->mixed ? spmm_units<KP, true, R1>(c->n, c->n_heavy, c->n_chunks)
+                    : spmm_units<KP, false, R0>(c->n, c->n_heavy, c->n_chunks);
   }
+  static int64_t units(const cluster_ctx* c, int shape) {
+    return shape == 1 ? units_s<1>(c) : shape == 2 ? units_s<2>(c) : units_s<0>(c);
+  }
+  static int nb(bool mixed, int shape) {
+    if (mixed) return shape == 2 ? BShape<KP, true, 2>::NB : BShape<KP, true, 0>::NB;
+    return shape == 2 ? BShape<KP, false, 2>::NB : BShape<KP, false, 0>::NB;
+  }
+  static int rpu(int shape) { return shape == 1 ? BShape<KP, false, 1>::RPU : BShape<KP, false, 0>::RPU; }
   // one iteration with events around the two persistent kernels
-  static void timed_iteration(const BatchClass& bc, int spmm_grid, int upd_grid, cudaEvent_t* ev, cudaStream_t s) {
+  static void timed_iteration(const BatchClass& bc, int shape, int spmm_grid, int upd_grid, cudaEvent_t* ev,
+                              cudaStream_t s) {
     cudaMemsetAsync(bc.d_work, 0, 2 * sizeof(unsigned long long), s);
     cudaEventRecord(ev[0], s);
-    if (bc.mixed) batch_spmm_kernel<KP, true><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
-    else batch_spmm_kernel<KP, false><<<spmm_grid, L::NT, 0, s>>>(bc.meta);
+    spmm(bc, shape, spmm_grid, s);
     cudaEventRecord(ev[1], s);
     if (bc.heavy > 0) batch_finalize_kernel<KP><<<bc.fin_grid, 256, 0, s>>>(bc.meta);
     cudaEventRecord(ev[2], s);
@@ -145,8 +171,8 @@ static void batch_release_tables(cluster_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
   for (auto& bc : b->classes) {
-    void* ps[] = {bc.d_args, bc.d_folds, bc.d_unit_base, bc.d_heavy_base, bc.d_item_inst, bc.d_item_slot,
-                  bc.d_parts, bc.d_states, bc.d_work};
+    void* ps[] = {bc.d_args, bc.d_folds, bc.d_ub[0], bc.d_ub[1], bc.d_ub[2], bc.d_heavy_base, bc.d_item_inst,
+                  bc.d_item_slot, bc.d_parts, bc.d_states, bc.d_work};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
@@ -179,7 +205,8 @@ static cluster_status build_class(cluster_batch* b, BatchClass& bc, int sms) {
   cudaStream_t s = b->stream;
   std::vector<PassArgs> args;
   std::vector<FoldArgs> folds;
-  std::vector<int64_t> ubase(1, 0), hbase(1, 0);
+  std::vector<int64_t> ubase[kGatherShapes], hbase(1, 0);
+  for (auto& u : ubase) u.assign(1, 0);
   std::vector<int32_t> item_inst, item_slot, parts;
   std::vector<FistaState*> states;
   for (size_t j = 0; j < bc.members.size(); ++j) {
@@ -188,9 +215,11 @@ static cluster_status build_class(cluster_batch* b, BatchClass& bc, int sms) {
     FoldArgs f = make_fold_args(c, 0, 0);
     f.work = nullptr;  // the batch zeroes its own counters
     folds.push_back(f);
-    int64_t u = 0;
-    FC_BDISPATCH(bc.KP, u = Ops::units(c));
-    ubase.push_back(ubase.back() + u);
+    for (int sh = 0; sh < kGatherShapes; ++sh) {
+      int64_t u = 0;
+      FC_BDISPATCH(bc.KP, u = Ops::units(c, sh));
+      ubase[sh].push_back(ubase[sh].back() + u);
+    }
     hbase.push_back(hbase.back() + c->n_heavy);
     parts.push_back(c->parts_upd);
     for (int sl = 0; sl < c->parts_upd; ++sl) {
@@ -199,12 +228,14 @@ static cluster_status build_class(cluster_batch* b, BatchClass& bc, int sms) {
     }
     states.push_back(c->st);
   }
-  bc.units = ubase.back();
+  for (int sh = 0; sh < kGatherShapes; ++sh) bc.units_s[sh] = ubase[sh].back();
+  bc.units = bc.units_s[0];
   bc.heavy = hbase.back();
   bc.n_items = (int)item_inst.size();
   FC_TRY(upload(&bc.d_args, args, s));
   FC_TRY(upload(&bc.d_folds, folds, s));
-  FC_TRY(upload(&bc.d_unit_base, ubase, s));
+  for (int sh = 0; sh < kGatherShapes; ++sh) FC_TRY(upload(&bc.d_ub[sh], ubase[sh], s));
+  bc.d_unit_base = bc.d_ub[0];
   FC_TRY(upload(&bc.d_heavy_base, hbase, s));
   FC_TRY(upload(&bc.d_item_inst, item_inst, s));
   FC_TRY(upload(&bc.d_item_slot, item_slot, s));
@@ -393,12 +424,14 @@ extern "C" cluster_status cluster_batch_get_U(cluster_batch* b, int32_t i, float
   return cluster_get_U(b->inst[i], U_out);
 }
 
-// Launch shapes of the two persistent kernels per class, chosen by timing.
-// Candidates: 1..occupancy resident blocks per SM for the gather kernel, then
-// for the update kernel (with the best gather shape).  Every trial is a real
-// iteration of all unfinished instances; a launch shape changes no value
-// (work units and update items are fixed per instance), so tuning does not
-// perturb the solve.  The graph is re-captured with the chosen shapes.
+// Tile and launch shapes per class, chosen by timing.  The gather's
+// candidates are its tile shapes (BShape: nonzeros per batch, rows per work
+// unit) times 1..occupancy resident blocks per SM; then the update kernel's
+// 1..occupancy blocks per SM with the chosen gather.  Every trial is a real
+// iteration of all unfinished instances; no shape changes a value (each row is
+// summed by one team in index order, update items are the instances' solo
+// blocks), so tuning does not perturb the solve.  The graph is re-captured
+// with the chosen shapes.
 extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trials) {
   clear_error();
   if (!b) FC_EINVAL("batch is NULL");
@@ -408,32 +441,50 @@ extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trial
   FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
   const int m = (int)b->inst.size();
   const int ncls = (int)b->classes.size();
+  std::vector<int> ng(ncls);  // gather candidates of each class
   int max_cand = 1;
-  for (auto& bc : b->classes) max_cand = std::max(max_cand, bc.occ_spmm + bc.occ_upd);
-  std::vector<std::vector<double>> t_spmm(ncls), t_upd(ncls);
+  for (int ci = 0; ci < ncls; ++ci) {
+    const BatchClass& bc = b->classes[ci];
+    ng[ci] = kGatherShapes * bc.occ_spmm;
+    max_cand = std::max(max_cand, ng[ci] + bc.occ_upd);
+  }
+  auto gather_grid = [&](const BatchClass& bc, int shape, int per_sm) {
+    int warps = 8;
+    FC_BDISPATCH(bc.KP, warps = Ops::L::WARPS);
+    const int64_t bmax = std::max<int64_t>(1, (bc.units_s[shape] + warps - 1) / warps);
+    return (int)std::min<int64_t>((int64_t)sms * per_sm, bmax);
+  };
   std::vector<cudaEvent_t> ev((size_t)ncls * 4);
   for (auto& e : ev) FC_CUDA(cudaEventCreate(&e));
-  std::vector<int> best_s(ncls), best_u(ncls);
+  std::vector<int> best_s(ncls), best_u(ncls), best_sh(ncls);
+  std::vector<double> best_g(ncls, 1e30), best_t(ncls, 1e30), cur(ncls, 1e30);
   for (int ci = 0; ci < ncls; ++ci) {
     best_s[ci] = b->classes[ci].spmm_grid;
     best_u[ci] = b->classes[ci].upd_grid;
+    best_sh[ci] = b->classes[ci].shape;
   }
   cluster_status st = CLUSTER_OK;
   for (int cand = 0; cand < max_cand && st == CLUSTER_OK; ++cand) {
+    std::fill(cur.begin(), cur.end(), 1e30);
+    std::vector<int> gs(ncls), gu(ncls), sh(ncls);
+    for (int ci = 0; ci < ncls; ++ci) {
+      const BatchClass& bc = b->classes[ci];
+      if (cand < ng[ci]) {
+        sh[ci] = cand / bc.occ_spmm;
+        gs[ci] = gather_grid(bc, sh[ci], cand % bc.occ_spmm + 1);
+        gu[ci] = bc.upd_grid;
+      } else {
+        const int cu = std::min(cand - ng[ci], bc.occ_upd - 1);
+        sh[ci] = best_sh[ci];
+        gs[ci] = best_s[ci];
+        gu[ci] = std::max(1, std::min(sms * (cu + 1), bc.n_items));
+      }
+    }
     for (int rep = 0; rep < trials && st == CLUSTER_OK; ++rep) {
       batch_set_limit_kernel<<<(m + 255) / 256, 256, 0, b->stream>>>(b->d_all_states, m, 1);
-      std::vector<int> gs(ncls), gu(ncls);
       for (int ci = 0; ci < ncls; ++ci) {
         BatchClass& bc = b->classes[ci];
-        if (cand < bc.occ_spmm) {
-          gs[ci] = (int)std::min<int64_t>((int64_t)sms * (cand + 1), bc.gather_blocks_max);
-          gu[ci] = bc.upd_grid;
-        } else {
-          const int cu = cand - bc.occ_spmm;
-          gs[ci] = best_s[ci];
-          gu[ci] = std::max(1, std::min(sms * (std::min(cu, bc.occ_upd - 1) + 1), bc.n_items));
-        }
-        FC_BDISPATCH(bc.KP, Ops::timed_iteration(bc, gs[ci], gu[ci], &ev[(size_t)ci * 4], b->stream));
+        FC_BDISPATCH(bc.KP, Ops::timed_iteration(bc, sh[ci], gs[ci], gu[ci], &ev[(size_t)ci * 4], b->stream));
       }
       cudaError_t e = cudaStreamSynchronize(b->stream);
       if (e != cudaSuccess) {
@@ -442,51 +493,40 @@ extern "C" cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trial
         break;
       }
       for (int ci = 0; ci < ncls; ++ci) {
-        BatchClass& bc = b->classes[ci];
         float ms_s = 0.f, ms_u = 0.f;
         cudaEventElapsedTime(&ms_s, ev[(size_t)ci * 4 + 0], ev[(size_t)ci * 4 + 1]);
         cudaEventElapsedTime(&ms_u, ev[(size_t)ci * 4 + 2], ev[(size_t)ci * 4 + 3]);
-        if (cand < bc.occ_spmm) {
-          t_spmm[ci].push_back(ms_s);
-          if (rep == trials - 1) {
-            // best over the candidates timed so far (min over its trials)
-            const size_t nc = t_spmm[ci].size() / trials;
-            double best = 1e30;
-            for (size_t c2 = 0; c2 < nc; ++c2) {
-              double mn = 1e30;
-              for (int r = 0; r < trials; ++r) mn = std::min(mn, t_spmm[ci][c2 * trials + r]);
-              if (mn < best) {
-                best = mn;
-                best_s[ci] = (int)std::min<int64_t>((int64_t)sms * (c2 + 1), bc.gather_blocks_max);
-                bc.gather_ms = mn;
-              }
-            }
-          }
-        } else if (cand - bc.occ_spmm < bc.occ_upd) {
-          t_upd[ci].push_back(ms_u);
-          if (rep == trials - 1) {
-            const size_t nc = t_upd[ci].size() / trials;
-            double best = 1e30;
-            for (size_t c2 = 0; c2 < nc; ++c2) {
-              double mn = 1e30;
-              for (int r = 0; r < trials; ++r) mn = std::min(mn, t_upd[ci][c2 * trials + r]);
-              if (mn < best) {
-                best = mn;
-                best_u[ci] = std::max(1, std::min(sms * ((int)c2 + 1), bc.n_items));
-                bc.update_ms = mn;
-              }
-            }
-          }
+        cur[ci] = std::min(cur[ci], (double)(cand < ng[ci] ? ms_s : ms_u));
+      }
+    }
+    if (st != CLUSTER_OK) break;
+    for (int ci = 0; ci < ncls; ++ci) {
+      BatchClass& bc = b->classes[ci];
+      if (cand < ng[ci]) {
+        if (cur[ci] < best_g[ci]) {
+          best_g[ci] = cur[ci];
+          best_sh[ci] = sh[ci];
+          best_s[ci] = gs[ci];
+          bc.gather_ms = cur[ci];
         }
+      } else if (cand - ng[ci] < bc.occ_upd && cur[ci] < best_t[ci]) {
+        best_t[ci] = cur[ci];
+        best_u[ci] = gu[ci];
+        bc.update_ms = cur[ci];
       }
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (st != CLUSTER_OK) return st;
   for (int ci = 0; ci < ncls; ++ci) {
-    b->classes[ci].spmm_grid = best_s[ci];
-    b->classes[ci].upd_grid = best_u[ci];
-    b->classes[ci].tuned = true;
+    BatchClass& bc = b->classes[ci];
+    bc.shape = best_sh[ci];
+    bc.d_unit_base = bc.d_ub[bc.shape];
+    bc.meta.unit_base = bc.d_unit_base;
+    bc.units = bc.units_s[bc.shape];
+    bc.spmm_grid = best_s[ci];
+    bc.upd_grid = best_u[ci];
+    bc.tuned = true;
   }
   FC_TRY(capture_batch_graph(b));
   return batch_read(b, nullptr);
@@ -499,13 +539,16 @@ extern "C" cluster_status cluster_batch_describe(cluster_batch* b, char* buf, si
   std::string out = "{\"instances\": " + std::to_string(b->inst.size()) + ", \"classes\": [";
   for (size_t ci = 0; ci < b->classes.size(); ++ci) {
     const BatchClass& bc = b->classes[ci];
-    char tmp[512];
+    int nbv = 0, rpu = 0;
+    FC_BDISPATCH(bc.KP, (nbv = Ops::nb(bc.mixed, bc.shape), rpu = Ops::rpu(bc.shape)));
+    char tmp[640];
     snprintf(tmp, sizeof(tmp),
              "%s{\"kp\": %d, \"mixed\": %d, \"instances\": %zu, \"gather_units\": %lld, \"chunked_rows\": %lld, "
-             "\"update_items\": %d, \"gather_blocks\": %d, \"update_blocks\": %d, \"tuned\": %d, "
+             "\"update_items\": %d, \"gather_shape\": %d, \"gather_nonzeros_per_batch\": %d, "
+             "\"gather_rows_per_unit\": %d, \"gather_blocks\": %d, \"update_blocks\": %d, \"tuned\": %d, "
              "\"gather_ms\": %.4f, \"update_ms\": %.4f}",
              ci ? ", " : "", bc.KP, bc.mixed ? 1 : 0, bc.members.size(), (long long)bc.units, (long long)bc.heavy,
-             bc.n_items, bc.spmm_grid, bc.upd_grid, bc.tuned ? 1 : 0, bc.gather_ms, bc.update_ms);
+             bc.n_items, bc.shape, nbv, rpu, bc.spmm_grid, bc.upd_grid, bc.tuned ? 1 : 0, bc.gather_ms, bc.update_ms);
     out += tmp;
   }
   out += "]}";

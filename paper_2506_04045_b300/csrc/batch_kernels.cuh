@@ -40,7 +40,20 @@ __device__ __forceinline__ bool instance_idle(const FistaState* st) {
   return vs->done || vs->pass >= vs->limit;
 }
 
-template <int KP, bool MIXED>
+// Gather tile shapes the batch autotuner chooses from, per class: nonzeros per
+// batch per row (NB) and rows per team per work unit (RPU).  Shape 0 is the
+// solo solver's; 1 takes single-row units (finer dynamic balance over many
+// small instances); 2 halves the batch (fewer idle lanes on short rows).  No
+// shape changes a value: every row is summed by one team in index order.
+constexpr int kGatherShapes = 3;
+template <int KP, bool MIXED, int S>
+struct BShape {
+  static constexpr int NB0 = WLay<KP, MIXED>::NB;
+  static constexpr int NB = S == 2 ? (NB0 > 1 ? NB0 / 2 : 1) : NB0;
+  static constexpr int RPU = S == 1 ? 1 : kRowsPerUnit;
+};
+
+template <int KP, bool MIXED, int S = 0>
 __global__ void __launch_bounds__(Lay<KP>::NT) batch_spmm_kernel(BatchMeta b) {
   const int lane = threadIdx.x & 31;
   const int64_t total = b.unit_base[b.m];
@@ -53,7 +66,8 @@ __global__ void __launch_bounds__(Lay<KP>::NT) batch_spmm_kernel(BatchMeta b) {
     const PassArgs& a = b.args[j];
     if (instance_idle(a.st)) continue;
     const int64_t pass = ((const volatile FistaState*)a.st)->pass;
-    spmm_unit<KP, MIXED>(a, pass, (int64_t)u - b.unit_base[j], lane);
+    spmm_unit<KP, MIXED, BShape<KP, MIXED, S>::NB, BShape<KP, MIXED, S>::RPU>(a, pass, (int64_t)u - b.unit_base[j],
+                                                                             lane);
   }
 }
 

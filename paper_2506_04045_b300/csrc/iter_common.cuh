@@ -240,6 +240,13 @@ struct WLay {
   static constexpr int PER = (NB + GT - 1) / GT; // (col, val) pairs each lane fetches per batch
 };
 
+// The layout with NBX nonzeros per batch per row (0 = WLay's NB).
+template <int KP, bool MIXED, int NBX>
+struct WShape : WLay<KP, MIXED> {
+  static constexpr int NB = NBX > 0 ? NBX : WLay<KP, MIXED>::NB;
+  static constexpr int PER = (NB + WLay<KP, MIXED>::GT - 1) / WLay<KP, MIXED>::GT;
+};
+
 // out[0 .. FEAT) = the LB bytes at p, widened to float
 template <int KP, bool MIXED>
 __device__ __forceinline__ void load_wide(const void* p, float* out) {
@@ -276,12 +283,14 @@ __device__ __forceinline__ void load_wide(const void* p, float* out) {
 
 // acc[0 .. FEAT) += sum_{e in [lo, hi)} val[e] * Xg[col[e], lt FEAT .. (lt+1) FEAT),
 // nonzeros in index order (the same order, and so the same sums, as gather).
-// `batches` must be the same on every lane of the warp.
-template <int KP, bool MIXED>
+// `batches` (batches of NBX nonzeros; 0 = the layout's NB) must be the same
+// on every lane of the warp.  The batch size changes no value: each row's sum
+// runs over its nonzeros in index order.
+template <int KP, bool MIXED, int NBX = 0>
 __device__ __forceinline__ void gather_wide(const int32_t* __restrict__ col, const void* __restrict__ valp,
                                             const void* __restrict__ Xg, int64_t lo, int64_t hi, int batches,
                                             int lt, float* acc) {
-  using W = WLay<KP, MIXED>;
+  using W = WShape<KP, MIXED, NBX>;
   using VT = typename GatherT<MIXED>::V;
   const VT* val = reinterpret_cast<const VT*>(valp);
   const char* xb = reinterpret_cast<const char*>(Xg) + lt * W::LB;

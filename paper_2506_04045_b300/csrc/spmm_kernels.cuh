@@ -17,22 +17,25 @@ namespace fc {
 // schedule does not change any value.
 constexpr int kRowsPerUnit = 4;
 
-// Work units of one instance's gather: chunk units, then row units.
+// Work units of one instance's gather: chunk units, then row units of
+// TPW * RPU consecutive positions.
 template <int KP, bool MIXED>
 __host__ __device__ __forceinline__ int64_t spmm_chunk_units(int64_t n_chunks) {
   return (n_chunks + WLay<KP, MIXED>::TPW - 1) / WLay<KP, MIXED>::TPW;
 }
-template <int KP, bool MIXED>
+template <int KP, bool MIXED, int RPU = kRowsPerUnit>
 __host__ __device__ __forceinline__ int64_t spmm_units(int64_t n, int64_t n_heavy, int64_t n_chunks) {
-  const int64_t per = (int64_t)WLay<KP, MIXED>::TPW * kRowsPerUnit;
+  const int64_t per = (int64_t)WLay<KP, MIXED>::TPW * RPU;
   return spmm_chunk_units<KP, MIXED>(n_chunks) + (n - n_heavy + per - 1) / per;
 }
 
 // One warp processes gather unit u of an instance (see spmm_kernel); the
-// GT lanes of a row each own FEAT consecutive features of z.
-template <int KP, bool MIXED>
+// GT lanes of a row each own FEAT consecutive features of z.  Tile shape:
+// NBX nonzeros per batch (0 = the layout's), RPU rows per team per unit; the
+// shape changes no value (each row is summed by one team in index order).
+template <int KP, bool MIXED, int NBX = 0, int RPU = kRowsPerUnit>
 __device__ __forceinline__ void spmm_unit(const PassArgs& a, int64_t pass, int64_t u, int lane) {
-  using W = WLay<KP, MIXED>;
+  using W = WShape<KP, MIXED, NBX>;
   const float* P = (pass & 1) ? a.X1 : a.X0;
   const void* Xg = MIXED ? (const void*)((pass & 1) ? a.XS1 : a.XS0) : (const void*)P;
   float* Zc = ((pass + 1) & 1) ? a.Z1 : a.Z0;
@@ -46,25 +49,25 @@ __device__ __forceinline__ void spmm_unit(const PassArgs& a, int64_t pass, int64
 #pragma unroll
     for (int q = 0; q < W::FEAT; ++q) acc[q] = 0.f;
     const int batches = __reduce_max_sync(kFull, (int)((hi - lo + W::NB - 1) / W::NB));
-    gather_wide<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, acc);
+    gather_wide<KP, MIXED, W::NB>(a.col, a.val, Xg, lo, hi, batches, lt, acc);
     if (act) store_feats<W::FEAT>(a.hv_part + c * KP + f0, acc);
     return;
   }
-  const int64_t base = a.n_heavy + (u - n_cu) * W::TPW * kRowsPerUnit;
+  const int64_t base = a.n_heavy + (u - n_cu) * W::TPW * RPU;
   int64_t nrow = (base + tiw < a.n) ? (int64_t)a.order[base + tiw] : 0;
 #pragma unroll 1
-  for (int m = 0; m < kRowsPerUnit; ++m) {
+  for (int m = 0; m < RPU; ++m) {
     const int64_t pos = base + (int64_t)m * W::TPW + tiw;
     const bool act = pos < a.n;
     const int64_t row = nrow;
     const int64_t npos = pos + W::TPW;
-    nrow = (m + 1 < kRowsPerUnit && npos < a.n) ? (int64_t)a.order[npos] : 0;
+    nrow = (m + 1 < RPU && npos < a.n) ? (int64_t)a.order[npos] : 0;
     const int64_t lo = act ? a.row_ptr[row] : 0, hi = act ? a.row_ptr[row + 1] : 0;
     float acc[W::FEAT];
 #pragma unroll
     for (int q = 0; q < W::FEAT; ++q) acc[q] = 0.f;
     const int batches = __reduce_max_sync(kFull, (int)((hi - lo + W::NB - 1) / W::NB));
-    gather_wide<KP, MIXED>(a.col, a.val, Xg, lo, hi, batches, lt, acc);
+    gather_wide<KP, MIXED, W::NB>(a.col, a.val, Xg, lo, hi, batches, lt, acc);
     if (act) store_feats<W::FEAT>(Zc + row * KP + f0, acc);
   }
 }

@@ -11,15 +11,17 @@
 // Xbar^n and of Y^{n+1} = Xbar^n + beta_{n+1} (Xbar^n - Xbar^{n-1}).
 //
 // Layout and roles (one CTA per SM, persistent over a contiguous range of
-// tiles; 288 threads):
+// tiles; 320 threads):
 //   * two compute warpgroups (warps 0-3 and 4-7) take the CTA's tiles in turn;
 //     thread t of a warpgroup owns row t of its tile and keeps the row's 32
 //     features in registers, so the projection, the trace term and the norm
 //     are sums inside one thread (no shuffles);
-//   * one helper thread (warp 8) issues the TMA loads of the four input tiles
-//     (z, xbar^{n-1}, xbar^{n-2}, z^{prev}: 4 x 16 KB, 128-byte swizzle, which
-//     makes every thread's 16-byte reads of its own row conflict-free) and all
-//     tcgen05.mma instructions, polling the warpgroups' mbarriers.
+//   * one helper thread per warpgroup (warps 8 and 9) issues its TMA loads of
+//     the four input tiles (z, xbar^{n-1}, xbar^{n-2}, z^{prev}: 4 x 16 KB,
+//     128-byte swizzle, which makes every thread's 16-byte reads of its own
+//     row conflict-free) and its tcgen05.mma instructions, sleeping in
+//     mbarrier waits between them (no polling loop taking issue slots from
+//     the compute warps).
 //   * y G(Y): kind::tf32, 3xTF32 (hi/lo split), M = 128 = the tile's rows, so
 //     row r of the accumulator is TMEM lane r and each thread reads its own
 //     row back (tcgen05.ld 32x32b).  The y operand (hi, lo) goes to the
@@ -60,7 +62,7 @@ struct StreamMaps {
 namespace ts {
 
 constexpr int R = 128;                  // rows per tile
-constexpr int NT = 288;                 // 2 x 128 compute threads + one helper warp
+constexpr int NT = 320;                 // 2 x 128 compute threads + one helper warp per warpgroup
 constexpr int TILE_B = R * 128;         // one tile of one input: 16 KB
 constexpr int STAGE_B = 4 * TILE_B;     // z, xbar^{n-1}, xbar^{n-2}, z^{prev}
 constexpr int GOP_B = 2 * R * 128;      // Gram operand: h and l, 128 rows x 64 float16
@@ -75,10 +77,8 @@ constexpr int TMEM_COLS = 512;
 constexpr int COL_YG = 0, COL_GA = 64, COL_GB = 128, COL_ACC = 192, COL_PV = 224, COL_WG = 256;
 constexpr float kScale = 8192.0f;                          // 2^13
 constexpr float kUnscale2 = 1.0f / (8192.0f * 8192.0f);   // 2^-26, exact
-// mbarriers of warpgroup w: w * 5 + {full, yready, ygdone, gready, grdone}; [10] final commit
-constexpr int BAR_FULL = 0, BAR_YREADY = 1, BAR_YGDONE = 2, BAR_GREADY = 3, BAR_GRDONE = 4, NBARS = 11;
-// the helper gives up after this many idle rounds of at least kIdleNs (about one second)
-constexpr uint32_t kIdleRounds = 1u << 24, kIdleNs = 64u;
+// mbarriers of warpgroup w: w * 5 + {full, yready, ygdone, gready, grdone}; 10 + w: its helper's final commit
+constexpr int BAR_FULL = 0, BAR_YREADY = 1, BAR_YGDONE = 2, BAR_GREADY = 3, BAR_GRDONE = 4, NBARS = 12;
 
 static_assert(SMEM <= 232448, "shared memory of the streaming update");
 
@@ -135,14 +135,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
+// 32-byte store (one whole sector; p 32-byte aligned)
+__device__ __forceinline__ void st_v8(void* p, const uint32_t* v) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+               "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
 __device__ __forceinline__ void named_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// TMEM lane of the calling thread (32 lanes of its warp's quarter), 32
-// consecutive columns from taddr into v
-__device__ __forceinline__ void ld32x32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// TMEM -> registers, no wait: the calling thread's lane (of its warp's
+// quarter), 32 consecutive columns from taddr; the values may be used only
+// after wait_ld().  Several loads can be in flight under one wait.
+__device__ __forceinline__ void ld32x32_async(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -151,15 +157,30 @@ __device__ __forceinline__ void ld32x32(uint32_t taddr, float* v) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
-// the inverse: 32 consecutive columns of the calling thread's lane from v
-__device__ __forceinline__ void st32x32(uint32_t taddr, const float* v) {
-  uint32_t r[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(v[j]);
+// 16 lanes x 16 columns (shape 16x32bx2, half offset 8), no wait: thread t gets
+// lane base + (t & 15), columns col + 8 (t >> 4) + j, j < 8
+__device__ __forceinline__ void ld16x16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], 8;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After wait_ld(): make every later use of the loaded registers depend on a
+// point ordered after the wait (an empty volatile asm that "rewrites" them),
+// so the compiler cannot move a use above the wait.
+__device__ __forceinline__ void pin8(uint32_t* r) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+__device__ __forceinline__ void pin32(uint32_t* r) {
+  pin8(r);
+  pin8(r + 8);
+  pin8(r + 16);
+  pin8(r + 24);
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// registers -> TMEM, no wait (wait_st() before the columns are read again)
+__device__ __forceinline__ void st32x32_async(uint32_t taddr, const uint32_t* r) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
       "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
@@ -168,7 +189,6 @@ __device__ __forceinline__ void st32x32(uint32_t taddr, const float* v) {
       "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
       "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Shared state of one CTA of the streaming update.
@@ -184,13 +204,13 @@ struct StreamCta {
   __device__ __forceinline__ bool aborted() const { return *reinterpret_cast<volatile int*>(flags) != 0; }
 };
 
-// The helper thread: TMA loads into a warpgroup's stage once the warpgroup
-// has read its previous tile's rows (its y-ready arrival), y G once the
-// warpgroup has written its y operand, the Gram once it has written the Gram
-// operand.  The three chains of both warpgroups are polled in turn, so
-// neither warpgroup waits for the other.  Returns after every issued load
-// has landed and every issued MMA has completed (each bounded).
-__device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMaps& m, int64_t pass) {
+// The helper thread of warpgroup w, in the warpgroup's order: the first
+// tile's loads; then per tile, once the warpgroup has read its rows and
+// written its y operand (y-ready): the next tile's loads into the freed stage
+// and y G; once it has written the Gram operand (G-ready): the Gram.  Every
+// wait is bounded and also ends on the abort flag.  Returns after its issued
+// loads have landed and its MMAs have completed (each bounded).
+__device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMaps& m, int64_t pass, int w) {
   const CUtensorMap* mz = &m.Z[(pass + 1) & 1];   // S Xbar^{pass}
   const CUtensorMap* mp = &m.X[pass & 1];         // Xbar^{pass}
   const CUtensorMap* mq = &m.X[(pass + 1) & 1];   // Xbar^{pass-1}
@@ -200,85 +220,79 @@ __device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMa
   prefetch_map(mq);
   prefetch_map(mzp);
   const bool hook = (c.flags[1] & 1) != 0;
-  const int ntw[2] = {(c.cnt + 1) / 2, c.cnt / 2};
-  int nl[2] = {0, 0}, ny[2] = {0, 0}, ng[2] = {0, 0};
-  uint32_t idle = 0;
-  for (;;) {
-    bool all = true, prog = false;
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      if (ng[w] < ntw[w]) all = false;
-      const uint32_t st = c.sb + OFF_WG + (uint32_t)w * WG_B;
-      // load the warpgroup's next tile once the stage is free
-      if (nl[w] < ntw[w] && (nl[w] == 0 || test_wait(c.bar(w, BAR_YREADY), (uint32_t)(nl[w] - 1) & 1u))) {
-        const int row = (int)((c.t0 + 2 * nl[w] + w) * R);
-        const uint32_t full = c.bar(w, BAR_FULL);
-        expect_tx(full, STAGE_B);
-        tma_load_2d(st + 0 * TILE_B, mz, 0, row, full);
-        tma_load_2d(st + 1 * TILE_B, mp, 0, row, full);
-        tma_load_2d(st + 2 * TILE_B, mq, 0, row, full);
-        tma_load_2d(st + 3 * TILE_B, mzp, 0, row, full);
-        ++nl[w];
-        prog = true;
-      }
-      // y G(Y): A = y hi / lo (in the Gram operand's area), B = G(Y) hi / lo
-      if (ny[w] < nl[w] && test_wait(c.bar(w, BAR_YREADY), (uint32_t)ny[w] & 1u)) {
-        tc::fence_after_sync();
-        const uint32_t d = c.tmem + (uint32_t)(w * COL_WG + COL_YG);
-        const uint32_t ya = st + STAGE_B;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ah = tc::desc_k128(ya + 32 * ks), al = tc::desc_k128(ya + TILE_B + 32 * ks);
-          const uint64_t bh = tc::desc_k128(c.sb + OFF_GH + 32 * ks), bl = tc::desc_k128(c.sb + OFF_GL + 32 * ks);
-          tc::mma(d, al, bh, idesc_tf32_m128(), ks > 0);
-          tc::mma(d, ah, bl, idesc_tf32_m128(), 1);
-          tc::mma(d, ah, bh, idesc_tf32_m128(), 1);
-        }
-        if (!hook) tc::commit(c.bar(w, BAR_YGDONE));
-        ++ny[w];
-        prog = true;
-      }
-      // Gram of [Xbar^n | Y^{n+1}] over the tile's rows (K = 128, 8 steps of 16)
-      if (ng[w] < ny[w] && test_wait(c.bar(w, BAR_GREADY), (uint32_t)ng[w] & 1u)) {
-        tc::fence_after_sync();
-        const uint32_t da = c.tmem + (uint32_t)(w * COL_WG + COL_GA), db = c.tmem + (uint32_t)(w * COL_WG + COL_GB);
-        const uint32_t g = st + STAGE_B;
-        constexpr uint32_t ID = idesc_f16_mn(64, 64);
-        // the small cross products first, then h h: rows 0-63 into A, 64-127 into B
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint64_t h = desc_mn128(g + 2048 * ks), l = desc_mn128(g + TILE_B + 2048 * ks);
-          mma_f16(da, l, h, ID, ks > 0);
-          mma_f16(da, h, l, ID, 1);
-        }
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint64_t h = desc_mn128(g + 2048 * ks);
-          if (ks < 4) mma_f16(da, h, h, ID, 1);
-          else mma_f16(db, h, h, ID, ks > 4);
-        }
-        tc::commit(c.bar(w, BAR_GRDONE));
-        ++ng[w];
-        prog = true;
-      }
+  const int ntw = (c.cnt + 1 - w) / 2;
+  const uint32_t st = c.sb + OFF_WG + (uint32_t)w * WG_B;
+  const uint32_t full = c.bar(w, BAR_FULL);
+  auto load = [&](int jj) {
+    const int row = (int)((c.t0 + 2 * jj + w) * R);
+    expect_tx(full, STAGE_B);
+    tma_load_2d(st + 0 * TILE_B, mz, 0, row, full);
+    tma_load_2d(st + 1 * TILE_B, mp, 0, row, full);
+    tma_load_2d(st + 2 * TILE_B, mq, 0, row, full);
+    tma_load_2d(st + 3 * TILE_B, mzp, 0, row, full);
+  };
+  auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+    for (uint32_t i = 0; i < tc::kWaitPolls; ++i) {
+      if (tc::bar_try(bar, par)) return true;
+      if (c.aborted()) return false;
     }
-    if (all) break;
-    if (prog) {
-      idle = 0;
-    } else {
-      if (c.aborted() || ++idle > kIdleRounds) {
-        *reinterpret_cast<volatile int*>(c.flags) = 1;
-        break;
+    *reinterpret_cast<volatile int*>(c.flags) = 1;
+    return false;
+  };
+  int nl = 0;
+  if (ntw > 0) {
+    load(0);
+    nl = 1;
+  }
+  for (int jj = 0; jj < ntw; ++jj) {
+    if (!wait(c.bar(w, BAR_YREADY), (uint32_t)jj & 1u)) break;
+    if (jj + 1 < ntw) {
+      load(jj + 1);
+      ++nl;
+    }
+    // y G(Y): A = y hi / lo (in the Gram operand's area), B = G(Y) hi / lo
+    tc::fence_after_sync();
+    {
+      const uint32_t d = c.tmem + (uint32_t)(w * COL_WG + COL_YG);
+      const uint32_t ya = st + STAGE_B;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ah = tc::desc_k128(ya + 32 * ks), al = tc::desc_k128(ya + TILE_B + 32 * ks);
+        const uint64_t bh = tc::desc_k128(c.sb + OFF_GH + 32 * ks), bl = tc::desc_k128(c.sb + OFF_GL + 32 * ks);
+        tc::mma(d, al, bh, idesc_tf32_m128(), ks > 0);
+        tc::mma(d, ah, bl, idesc_tf32_m128(), 1);
+        tc::mma(d, ah, bh, idesc_tf32_m128(), 1);
       }
-      __nanosleep(kIdleNs);
+      if (!hook) tc::commit(c.bar(w, BAR_YGDONE));
+    }
+    if (!wait(c.bar(w, BAR_GREADY), (uint32_t)jj & 1u)) break;
+    // Gram of [Xbar^n | Y^{n+1}] over the tile's rows (K = 128, 8 steps of 16):
+    // the small cross products first, then h h: rows 0-63 into A, 64-127 into B
+    tc::fence_after_sync();
+    {
+      const uint32_t da = c.tmem + (uint32_t)(w * COL_WG + COL_GA), db = c.tmem + (uint32_t)(w * COL_WG + COL_GB);
+      const uint32_t g = st + STAGE_B;
+      constexpr uint32_t ID = idesc_f16_mn(64, 64);
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint64_t h = desc_mn128(g + 2048 * ks), l = desc_mn128(g + TILE_B + 2048 * ks);
+        mma_f16(da, l, h, ID, ks > 0);
+        mma_f16(da, h, l, ID, 1);
+      }
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint64_t h = desc_mn128(g + 2048 * ks);
+        if (ks < 4) mma_f16(da, h, h, ID, 1);
+        else mma_f16(db, h, h, ID, ks > 4);
+      }
+      tc::commit(c.bar(w, BAR_GRDONE));
     }
   }
   // nothing of this thread may be in flight when the CTA exits
-  const uint32_t fin = c.bars + 8u * 10u;
+  const uint32_t fin = c.bars + 8u * (uint32_t)(10 + w);
   tc::commit(fin);
   tc::bar_wait(fin, 0);
-  for (int w = 0; w < 2; ++w)
-    if (nl[w] > 0) tc::bar_wait(c.bar(w, BAR_FULL), (uint32_t)(nl[w] - 1) & 1u);
+  if (nl > 0) tc::bar_wait(full, (uint32_t)(nl - 1) & 1u);
 }
 
 // One compute thread: row t of each tile of warpgroup w.  Per tile: the four
@@ -305,10 +319,10 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
   const uint32_t tw = c.tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(w * COL_WG);
   const int gm = qw >> 1;  // Gram rows of this warp's quarter: matrix 0 (Xbar^n) or 1 (Y^{n+1})
   {
-    float z[32];
+    uint32_t z[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) z[i] = 0.f;
-    st32x32(tw + COL_ACC, z);  // running Gram partial: [0, 16) high parts, [16, 32) low parts
+    for (int i = 0; i < 32; ++i) z[i] = 0u;
+    st32x32_async(tw + COL_ACC, z);  // running Gram partial: [0, 16) high parts, [16, 32) low parts
   }
   float tr_hi = 0.f, tr_lo = 0.f, pg_hi = 0.f, pg_lo = 0.f;
   int bad = 0;
@@ -331,21 +345,29 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     tc::fence_after_sync();
     return ok;
   };
-  // the previous tile's Gram (both accumulators) into the float pairs
+  // the previous tile's Gram (both accumulators) into the float pairs: all
+  // TMEM loads under one wait, the store's completion awaited only before the
+  // next load of the same columns
   auto gram_back = [&]() {
-    float g[32];
-    ld32x32(tw + COL_ACC, g);
+    uint32_t g[32], v[4][8];
+    wait_st();
+    ld32x32_async(tw + COL_ACC, g);
 #pragma unroll
-    for (int acc = 0; acc < 2; ++acc) {
+    for (int acc = 0; acc < 2; ++acc)
 #pragma unroll
-      for (int cg = 0; cg < 2; ++cg) {
-        float v[8];
-        tc::ld16x16(tw + (acc ? COL_GB : COL_GA) + 32 * gm + 16 * cg, v);
+      for (int cg = 0; cg < 2; ++cg) ld16x16_async(tw + (acc ? COL_GB : COL_GA) + 32 * gm + 16 * cg, v[2 * acc + cg]);
+    wait_ld();
+    pin32(g);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) two_sum_acc(g[8 * cg + j], g[16 + 8 * cg + j], v[j]);
-      }
-    }
-    st32x32(tw + COL_ACC, g);
+    for (int i = 0; i < 4; ++i) pin8(v[i]);
+    float* gf = reinterpret_cast<float*>(g);
+#pragma unroll
+    for (int acc = 0; acc < 2; ++acc)
+#pragma unroll
+      for (int cg = 0; cg < 2; ++cg)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) two_sum_acc(gf[8 * cg + j], gf[16 + 8 * cg + j], __uint_as_float(v[2 * acc + cg][j]));
+    st32x32_async(tw + COL_ACC, g);
   };
 
   for (int jj = 0; jj < ntw; ++jj) {
@@ -359,7 +381,7 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
       gram_back();
     }
     float y[32], sy[32], pv[32];
-    float d = 0.f;
+    float dq[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums: short dependency chains
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
       const int off = t * 128 + ((ch ^ swz) << 4);
@@ -373,14 +395,20 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
       for (int q = 0; q < 4; ++q) {
         const int f = 4 * ch + q;
         pv[f] = pvv[q];
-        d = fmaf(pvv[q], zv[q], d);
+        dq[q] = fmaf(pvv[q], zv[q], dq[q]);
         y[f] = fmaf(beta, pvv[q] - qv[q], pvv[q]);
         sy[f] = fmaf(beta, zv[q] - zp[q], zv[q]);
       }
       // y operand (row t, 128-byte swizzle, K-major): hi, lo
       split_store4(reinterpret_cast<float*>(gp + off), reinterpret_cast<float*>(gp + TILE_B + off), &y[4 * ch]);
     }
-    st32x32(tw + COL_PV, pv);
+    {
+      uint32_t pu[32];
+#pragma unroll
+      for (int f = 0; f < 32; ++f) pu[f] = __float_as_uint(pv[f]);
+      st32x32_async(tw + COL_PV, pu);
+    }
+    const float d = (dq[0] + dq[1]) + (dq[2] + dq[3]);
     if (!isfinite(d)) bad = 1;  // d is finite exactly when every z of the row is
     if (active) two_sum_acc(tr_hi, tr_lo, d);
     tc::fence_smem_to_async();
@@ -389,13 +417,25 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     if (!wait(c.bar(w, BAR_YGDONE), (uint32_t)jj & 1u)) break;
 
     float v[32];
-    ld32x32(tw + COL_YG, v);  // (y G(Y))_i of this row
-    float s = 0.f;
+    {
+      uint32_t qu[32];
+      ld32x32_async(tw + COL_YG, qu);  // (y G(Y))_i of this row
+      wait_ld();
+      pin32(qu);
+#pragma unroll
+      for (int f = 0; f < 32; ++f) v[f] = __uint_as_float(qu[f]);
+    }
+    float sq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int f = 0; f < 32; ++f) {
       v[f] = fmaf(tau4, sy[f] - v[f], y[f]);
-      s += v[f];  // padded features are exactly zero
+      sq[f & 3] += v[f];  // padded features are exactly zero
     }
+    const float s = (sq[0] + sq[1]) + (sq[2] + sq[3]);
+    // this row of xbar^{n-1} back from TMEM, landing while the row is projected
+    uint32_t pvu[32];
+    wait_st();
+    ld32x32_async(tw + COL_PV, pvu);
 #pragma unroll
     for (int f = 0; f < 32; ++f)
       if (f >= k) v[f] = -INFINITY;
@@ -403,47 +443,58 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     float cnt = (float)k;
     float theta = __fdividef(s - 1.0f, cnt);
     for (int it = 0; it <= 32; ++it) {
-      float s2 = 0.f, c2 = 0.f;
+      float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int f = 0; f < 32; ++f) {
         const bool on = v[f] > theta;
-        s2 += on ? v[f] : 0.f;
-        c2 += on ? 1.f : 0.f;
+        s4[f & 3] += on ? v[f] : 0.f;
+        c4[f & 3] += on ? 1.f : 0.f;
       }
+      const float s2 = (s4[0] + s4[1]) + (s4[2] + s4[3]), c2 = (c4[0] + c4[1]) + (c4[2] + c4[3]);
       if (c2 == cnt) break;
       cnt = c2;
       theta = __fdividef(s2 - 1.0f, cnt);
     }
-    float pg = 0.f;
+    float pq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int f = 0; f < 32; ++f) {
       v[f] = fmaxf(v[f] - theta, 0.0f);  // xbar^n_i
       const float dd = y[f] - v[f];
-      pg = fmaf(dd, dd, pg);
+      pq[f & 3] = fmaf(dd, dd, pq[f & 3]);
     }
+    const float pg = (pq[0] + pq[1]) + (pq[2] + pq[3]);
     if (!isfinite(pg)) bad = 1;
     if (active) {
       two_sum_acc(pg_hi, pg_lo, pg);
-      float4* xo = reinterpret_cast<float4*>(Qx + row * 32);
+      // whole 32-byte sectors: 4 stores per float32 row, 2 per bfloat16 row
+      float* xo = Qx + row * 32;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) xo[ch] = make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t u[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) u[e] = __float_as_uint(v[8 * ch + e]);
+        st_v8(xo + 8 * ch, u);
+      }
       if constexpr (MIXED) {
-        uint4* bo = reinterpret_cast<uint4*>(XSo + row * 32);
+        __nv_bfloat16* bo = XSo + row * 32;
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          uint32_t u[4];
+        for (int ch = 0; ch < 2; ++ch) {
+          uint32_t u[8];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * ch + 2 * e], v[8 * ch + 2 * e + 1]);
+          for (int e = 0; e < 8; ++e) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[16 * ch + 2 * e], v[16 * ch + 2 * e + 1]);
             u[e] = *reinterpret_cast<const uint32_t*>(&b2);
           }
-          bo[ch] = make_uint4(u[0], u[1], u[2], u[3]);
+          st_v8(bo + 16 * ch, u);
         }
       }
     }
     // the y operand has been read (y G completed): s [xbar^n | y^{n+1}] as
     // float16 h + l over it, row t, chunk ch = features 8 ch ..
-    ld32x32(tw + COL_PV, pv);
+    wait_ld();
+    pin32(pvu);
+#pragma unroll
+    for (int f = 0; f < 32; ++f) pv[f] = __uint_as_float(pvu[f]);
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
       uint32_t hu[4], lu[4];
@@ -501,7 +552,15 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
   constexpr int E2 = 32 * 32;
   const int r = 16 * (qw & 1) + (lane & 15);
   float g[32];
-  ld32x32(tw + COL_ACC, g);
+  {
+    uint32_t gu[32];
+    wait_st();
+    ld32x32_async(tw + COL_ACC, gu);
+    wait_ld();
+    pin32(gu);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) g[j] = __uint_as_float(gu[j]);
+  }
 #pragma unroll
   for (int cg = 0; cg < 2; ++cg) {
     const size_t o = (size_t)gm * E2 + (size_t)r * 32 + 16 * cg + 8 * (lane >> 4);
@@ -560,6 +619,7 @@ __global__ void __launch_bounds__(ts::NT, 1) update_stream_kernel(PassArgs a, co
       bar_init_n(c.bar(w, BAR_GRDONE), 1);
     }
     bar_init_n(c.bars + 8u * 10u, 1);
+    bar_init_n(c.bars + 8u * 11u, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     flags[0] = 0;
     flags[1] = vs->hooks;
@@ -580,7 +640,7 @@ __global__ void __launch_bounds__(ts::NT, 1) update_stream_kernel(PassArgs a, co
   if (warp < 8) {
     stream_compute<MIXED>(a, c, pass, 4 * (int)blockIdx.x, red);
   } else {
-    if ((tid & 31) == 0) stream_helper(c, maps, pass);
+    if ((tid & 31) == 0) stream_helper(c, maps, pass, warp - 8);
     __syncwarp();
   }
   tc::fence_before_sync();

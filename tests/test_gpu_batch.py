@@ -62,17 +62,21 @@ def test_batch_equals_solo_bitwise(precision):
 
 
 def test_autotuned_batch_still_equals_solo():
+    # every tuning trial is a real iteration with a candidate gather tile shape
+    # (nonzeros per batch, rows per work unit) and launch shape: a shape that
+    # changed any value would show in the bitwise comparison with solo runs
     inst = _instances(MIXED_SPECS[:7])
-    opts = dict(stop_rule=pkg.STOP_NONE, max_iter=60)
+    opts = dict(stop_rule=pkg.STOP_NONE, max_iter=120)
     b = pkg.Batch(inst, **opts)
     desc = b.autotune(trials=1)
     assert all(c["tuned"] == 1 for c in desc["classes"])
+    assert all(c["gather_nonzeros_per_batch"] >= 1 and c["gather_rows_per_unit"] >= 1 for c in desc["classes"])
     done = b.step(0)[0]["iters"]
-    assert 0 < done < 40
-    b.step(40 - done)
+    assert 0 < done < 100
+    b.step(100 - done)
     for i, (rp, c, v, U0) in enumerate(inst):
         s = pkg.Solver(rp, c, v, U0, **opts)
-        s.step(40)
+        s.step(100)
         assert torch.equal(b.get_U(i), s.get_U()), i
         s.close()
     b.close()

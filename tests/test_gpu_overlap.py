@@ -40,8 +40,10 @@ def test_overlapped_pass_equals_plain_pass_bitwise(k, precision):
     spec = synth.GraphSpec("dcsbm", 1_100_011, k, 500 + k, mean_deg=16.0)
     rp, c, v = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(spec.n, k, 500 + k, device="cuda")
-    Uo, ro, kto = _solve(rp, c, v, U0, 10, 3, precision=precision, overlap=1)
-    Up, rp_, ktp = _solve(rp, c, v, U0, 10, 3, precision=precision, overlap=0)
+    # the overlapped pass cuts the per-block update (engine 2) into chunks; the
+    # plain pass of the same engine is its reference
+    Uo, ro, kto = _solve(rp, c, v, U0, 10, 3, precision=precision, overlap=1, update_engine=2)
+    Up, rp_, ktp = _solve(rp, c, v, U0, 10, 3, precision=precision, overlap=0, update_engine=2)
     assert ro["iters"] == rp_["iters"] == 13
     assert torch.equal(Uo, Up)
     assert ro["f"] == rp_["f"] and ro["pg_norm"] == rp_["pg_norm"] and ro["trace_SU"] == rp_["trace_SU"]
@@ -61,7 +63,9 @@ def test_batch_holding_an_overlapped_instance_equals_it_solo():
     b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=12)
     b.step(12)
     for i, (rp, c, v, U0) in enumerate(inst):
-        s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=12)
+        # a batch runs the per-block update (engine 2), also for instances of
+        # at least 2^17 articles that stream when alone
+        s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=12, update_engine=2)
         s.step(12)
         assert torch.equal(b.get_U(i), s.get_U()), i
         s.close()
