@@ -591,6 +591,9 @@ def time_to_objective(args, pkg, rp, col, val, U0, ms_fp32, ms_mixed):
     rm = sm.solve() if it_f is None else sm.report()
     Um = sm.get_U()
     umax = float((Um - Uf).abs().max())
+    # the mixed form's loss is formed from its bfloat16 gathers; the objective of
+    # its iterate evaluated in float32 (cluster_objective) beside it
+    f_exact = pkg.objective(rp, col, val, Um)
     sm.close()
     del sm, Um, Uf
     torch.cuda.empty_cache()
@@ -606,6 +609,7 @@ def time_to_objective(args, pkg, rp, col, val, U0, ms_fp32, ms_mixed):
                   "it_s": (it_f + 1) / t_f if it_f is not None else None,
                   "seconds_from_rate": (it_f * ms_mixed / 1000.0) if it_f is not None else None,
                   "f_at_stop": rm["f"], "trace_at_stop": rm["trace_SU"],
+                  "f_float32_of_newest_iterate": f_exact, "f_float32_rel_to_f_star": (f_exact - f_star) / f_star,
                   "trace_rel_to_fp32": abs(rm["trace_SU"] - tr_star) / abs(tr_star),
                   "iterations_to_trace_within_1e-5": it_tr, "cap": cap},
         "max_abs_U_mixed_minus_fp32": umax,

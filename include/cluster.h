@@ -341,17 +341,21 @@ CLUSTER_API cluster_status cluster_batch_enqueue(cluster_batch* b, int64_t iters
  * (may be NULL). */
 CLUSTER_API cluster_status cluster_batch_step(cluster_batch* b, int64_t iters, cluster_report* reps);
 
-/* Choose the launch shapes (resident blocks per SM) of the batch's two
- * persistent kernels per class by timing candidates on live iterations:
- * each trial advances every unfinished instance by one iteration, exactly as
- * cluster_batch_step would (a launch shape changes no value).  About
- * trials x (sum over classes of the candidate count) iterations are used;
- * the CUDA graph is re-captured with the chosen shapes. */
+/* Choose, per class, the gather's tile shape (nonzeros per batch of a row,
+ * rows per work unit: three candidates, the first the solo solver's) and the
+ * launch shapes (resident blocks per SM) of the gather and the update by
+ * timing candidates on live iterations: each trial advances every unfinished
+ * instance by one iteration, exactly as cluster_batch_step would (no shape
+ * changes a value: each row is summed by one team in index order).  About
+ * trials x max over classes of (3 x gather occupancy + update occupancy)
+ * iterations are used; the CUDA graph is re-captured with the chosen shapes. */
 CLUSTER_API cluster_status cluster_batch_autotune(cluster_batch* b, int32_t trials);
 
-/* JSON description of the batch's classes and launch shapes into buf (after
- * cluster_batch_autotune also each class's gather and update times for the
- * chosen shapes, the class running alone, in milliseconds). */
+/* JSON description of the batch's classes into buf: per class the padded k,
+ * precision, instances, gather units, chunked rows, update items, the gather
+ * tile shape (shape index, nonzeros per batch, rows per unit) and the launch
+ * shapes; after cluster_batch_autotune also each class's gather and update
+ * times for the chosen shapes, the class running alone, in milliseconds. */
 CLUSTER_API cluster_status cluster_batch_describe(cluster_batch* b, char* buf, size_t len);
 
 /* Copy instance i's output iterate into U_out (device, n_i x k_i). */

@@ -30,8 +30,9 @@
 //     has read its rows: the next tile's loads overlap y G and the projection.
 //   * Gram of [Xbar^n | Y^{n+1}] (64 features): kind::f16 with both operands
 //     MN-major, i.e. the row-major tile itself (no transpose).  Each value is
-//     scaled by 2^13 and split into two float16 parts h + l (h = f16(s x),
-//     l = f16(s x - h)); h h + h l + l h carries the product to about 2^-22
+//     scaled by 2^13 and split into two float16 parts h + l (h = s x rounded
+//     to 11 significant bits, l = f16(s x - h)); h h + h l + l h carries the
+//     product to about 2^-22
 //     relative, like 3xTF32, and values below the float16 normal range lose
 //     only an absolute 2^-38 after the scale.  The accumulator is read back
 //     per tile and added into float pairs (TwoSum) in the threads, so the
@@ -135,6 +136,35 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
+// b rounded to 11 significant bits (the sign, 8 exponent and 10 stored
+// fraction bits of TF32), to nearest with ties away from zero, in integer
+// arithmetic: add half of the 13 dropped bits' weight, then drop them.  The
+// rounding cvt.rna.tf32.f32 performs, without the conversion pipe.
+__device__ __forceinline__ uint32_t round11(uint32_t b) { return (b + 0x1000u) & 0xFFFFE000u; }
+// 3xTF32 split of four values: hi = round11(x), lo = round11(x - hi)
+__device__ __forceinline__ void split11_store4(float* hi, float* lo, const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = round11(__float_as_uint(v[q]));
+    l[q] = round11(__float_as_uint(v[q] - __uint_as_float(h[q])));
+  }
+  *reinterpret_cast<uint4*>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// float pairs g[8 CG + j] (high) / g[16 + 8 CG + j] (low), kept as bits, += v[j]
+template <int CG>
+__device__ __forceinline__ void pair_acc8(uint32_t (&g)[32], const uint32_t (&v)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float h = __uint_as_float(g[8 * CG + j]), l = __uint_as_float(g[16 + 8 * CG + j]);
+    two_sum_acc(h, l, __uint_as_float(v[j]));
+    g[8 * CG + j] = __float_as_uint(h);
+    g[16 + 8 * CG + j] = __float_as_uint(l);
+  }
+}
+
 // 32-byte store (one whole sector; p 32-byte aligned)
 __device__ __forceinline__ void st_v8(void* p, const uint32_t* v) {
   asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
@@ -348,25 +378,38 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
   // the previous tile's Gram (both accumulators) into the float pairs: all
   // TMEM loads under one wait, the store's completion awaited only before the
   // next load of the same columns
+  // (warps holding Gram rows 16-31 of a block skip its columns 0-15: entries
+  // below the diagonal, which the fold never reads)
+  const bool below = (qw & 1) != 0;
   auto gram_back = [&]() {
-    uint32_t g[32], v[4][8];
+    uint32_t g[32], v0[8], v1[8], v2[8], v3[8];
     wait_st();
     ld32x32_async(tw + COL_ACC, g);
-#pragma unroll
-    for (int acc = 0; acc < 2; ++acc)
-#pragma unroll
-      for (int cg = 0; cg < 2; ++cg) ld16x16_async(tw + (acc ? COL_GB : COL_GA) + 32 * gm + 16 * cg, v[2 * acc + cg]);
-    wait_ld();
-    pin32(g);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) pin8(v[i]);
-    float* gf = reinterpret_cast<float*>(g);
-#pragma unroll
-    for (int acc = 0; acc < 2; ++acc)
-#pragma unroll
-      for (int cg = 0; cg < 2; ++cg)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) two_sum_acc(gf[8 * cg + j], gf[16 + 8 * cg + j], __uint_as_float(v[2 * acc + cg][j]));
+    if (below) {
+      ld16x16_async(tw + COL_GA + 32 * gm + 16, v1);
+      ld16x16_async(tw + COL_GB + 32 * gm + 16, v3);
+      wait_ld();
+      pin32(g);
+      pin8(v1);
+      pin8(v3);
+      pair_acc8<1>(g, v1);
+      pair_acc8<1>(g, v3);
+    } else {
+      ld16x16_async(tw + COL_GA + 32 * gm, v0);
+      ld16x16_async(tw + COL_GA + 32 * gm + 16, v1);
+      ld16x16_async(tw + COL_GB + 32 * gm, v2);
+      ld16x16_async(tw + COL_GB + 32 * gm + 16, v3);
+      wait_ld();
+      pin32(g);
+      pin8(v0);
+      pin8(v1);
+      pin8(v2);
+      pin8(v3);
+      pair_acc8<0>(g, v0);
+      pair_acc8<1>(g, v1);
+      pair_acc8<0>(g, v2);
+      pair_acc8<1>(g, v3);
+    }
     st32x32_async(tw + COL_ACC, g);
   };
 
@@ -400,7 +443,7 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
         sy[f] = fmaf(beta, zv[q] - zp[q], zv[q]);
       }
       // y operand (row t, 128-byte swizzle, K-major): hi, lo
-      split_store4(reinterpret_cast<float*>(gp + off), reinterpret_cast<float*>(gp + TILE_B + off), &y[4 * ch]);
+      split11_store4(reinterpret_cast<float*>(gp + off), reinterpret_cast<float*>(gp + TILE_B + off), &y[4 * ch]);
     }
     {
       uint32_t pu[32];
@@ -500,17 +543,20 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
       uint32_t hu[4], lu[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        float val[2];
+        // h = the scaled value rounded to float16's 11 significant bits (exact
+        // in float16 in its normal range), l = the exact remainder
+        float hv[2], lv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int f = 8 * (ch & 3) + 2 * e + h;
           const float xv = v[f];
           const float g = ch < 4 ? xv : fmaf(beta_next, xv - pv[f], xv);
-          val[h] = active ? g * kScale : 0.f;
+          const float val = active ? g * kScale : 0.f;
+          hv[h] = __uint_as_float(round11(__float_as_uint(val)));
+          lv[h] = val - hv[h];
         }
-        const __half2 hh = __floats2half2_rn(val[0], val[1]);
-        const float2 hf = __half22float2(hh);
-        const __half2 ll = __floats2half2_rn(val[0] - hf.x, val[1] - hf.y);
+        const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
+        const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
         hu[e] = *reinterpret_cast<const uint32_t*>(&hh);
         lu[e] = *reinterpret_cast<const uint32_t*>(&ll);
       }
@@ -563,6 +609,7 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
   }
 #pragma unroll
   for (int cg = 0; cg < 2; ++cg) {
+    if (cg == 0 && below) continue;  // below the diagonal: never read by the fold
     const size_t o = (size_t)gm * E2 + (size_t)r * 32 + 16 * cg + 8 * (lane >> 4);
     float* hi = a.gram_part + (size_t)shi * 2 * E2 + o;
     float* lo = a.gram_part + (size_t)slo * 2 * E2 + o;
