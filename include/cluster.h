@@ -129,21 +129,22 @@ typedef struct cluster_options {
                           highest-degree articles in a persisting L2 window
                           (half the device's persisting maximum; default);
                           0 = no window.  A cache hint: no value changes.       */
-  int32_t update_engine; /* form of the row-local update for 17 <= k <= 32:
-                          0 = automatic (default): a solver of at least 2^17
-                          articles streams (3), smaller ones and batched or
-                          served instances use 2;
-                          1 = warp-level mma.sync, 64 x 64 blocks of rows;
+  int32_t update_engine; /* form of the row-local update for 17 <= k <= 64:
+                          0 = automatic (default): k <= 32 streams (3) on a
+                          solver of at least 2^17 articles and uses 2 otherwise
+                          (batched and served instances too); 33 <= k <= 64
+                          uses 1 (measured faster there);
+                          1 = warp-level mma.sync, blocks of rows;
                           2 = tcgen05.mma with TMEM accumulators, the same
                           blocks, products and order as 1 (the same bits);
-                          3 = streaming: one CTA per SM over tiles of 128 rows
-                          moved by TMA, one thread per row, y G on tcgen05 as
-                          3xTF32 and the Gram matrices as scaled float16 splits
-                          with float-pair partials (results within float32
-                          rounding of 1 and 2, not the same bits); a batch or
-                          the overlapped pass uses 2 instead.
-                          Other k always use mma.sync (16 < k <= 64) or float32
-                          FMA.                                                   */
+                          3 = streaming (k <= 32): one CTA per SM over tiles of
+                          128 rows moved by TMA, one thread per row, y G on
+                          tcgen05 as 3xTF32 and the Gram matrices as scaled
+                          float16 splits with float-pair partials (results
+                          within float32 rounding of 1 and 2, not the same
+                          bits); a batch or the overlapped pass uses 2 instead.
+                          k <= 16 uses mma.sync (k > 8) or float32 FMA, k > 64
+                          float32 FMA.                                            */
   int32_t overlap;     /* 1 = with the internal numbering and n >= 2^20, run the
                           update of each of 8 row chunks on a second stream as
                           soon as the gather has produced that chunk's rows,

@@ -762,7 +762,11 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->parts = (int)parts;
   c->heavy_grid = sms * occ;
   c->split = opt.fused_pass == 0;
-  c->tc_update = opt.update_engine != 1;
+  // tcgen05 per-block update: engine 2 (and 3 where the streaming form does
+  // not apply) for k in 17..64; engine 0 for k in 17..32 only (for k in
+  // 33..64 the warp form measured faster: 2.9 vs 3.2 ms per batched iteration
+  // of the k = 64 class, the 16-row tiles being latency-bound)
+  c->tc_update = opt.update_engine == 2 || opt.update_engine == 3 || (opt.update_engine == 0 && c->KP <= 32);
   // streaming update for 17 <= k <= 32 on a solo split solver without the
   // overlapped pass: engine 0 from kStreamMinRows articles, engine 3 always
   c->stream_update = c->split && capture && c->KP == 32 && !opt.overlap &&

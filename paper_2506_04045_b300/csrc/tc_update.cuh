@@ -1,5 +1,6 @@
 // Row-local update of the split iteration on the fifth-generation tensor
-// cores (tcgen05, sm_103a) for KP = 32 (k <= 32).
+// cores (tcgen05, sm_103a) for KP = 32 (17 <= k <= 32) and KP = 64 (33 <= k
+// <= 64).
 //
 // Same arithmetic as update_kernel in pass_kernels.cuh, per row i:
 //   y_i  = xbar^{n-1}_i + beta (xbar^{n-1}_i - xbar^{n-2}_i)          (X^n, Alg. 4)
@@ -130,6 +131,23 @@ __device__ __forceinline__ void ld16x16(uint32_t taddr, float* v) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 32 TMEM lanes (this warp's quarter) x 32 columns: thread t gets lane base +
+// t, columns col .. col + 31
+__device__ __forceinline__ void ld32x32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16)
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -142,26 +160,36 @@ __device__ __forceinline__ int sw_chunk(int r, int c) { return r * 128 + ((c ^ (
 
 template <int KP>
 struct TcUpd {
-  static constexpr bool ON = FC_TC_UPDATE && KP == 32;
-  static constexpr int R = 32;  // tile rows (= Lay<32>::R)
-  // Gram operand (the transposed tile, 64 feature rows x 32 tile rows, hi and
-  // lo): K-major core matrices of 8 features x 4 tile rows; the one for
+  static constexpr bool ON = FC_TC_UPDATE && (KP == 32 || KP == 64);
+  static constexpr int R = Lay<KP>::R;  // tile rows: 32 (KP = 32), 16 (KP = 64)
+  // Operands in the K-major layout with 128-byte swizzle: a row of KP TF32
+  // values spans KP / 32 atoms of 128 bytes; atom a of all the rows first
+  // (the y tile: ATOM_Y bytes per atom; G(Y): ATOM_G), then atom a + 1.
+  static constexpr int ATOMS = KP / 32;
+  static constexpr int ATOM_Y = R * 128, ATOM_G = KP * 128;
+  // Gram operand (the transposed tile, 2 KP feature rows x R tile rows, hi
+  // and lo): K-major core matrices of 8 features x 4 tile rows; the one for
   // features 8 g.. and rows 4 c.. at g * CM_SBO + c * CM_LBO.  CM_SBO = 144
-  // (36 words = 4 mod 32) puts the stores of a warp (8 features x 4 rows per
-  // instruction) in 32 distinct banks.
-  static constexpr int CM_SBO = 144, CM_LBO = 8 * CM_SBO, TBYTES = 8 * CM_LBO;
-  // byte offsets from the 1024-aligned base: G hi / lo and Y hi / lo (128-byte
-  // swizzle; the M = 64 read of Y lo runs 4 KB into TH, rows that are ignored),
-  // the transposed tile hi / lo, the Y G staging rows (stride QS floats)
+  // (36 words = 4 mod 32) spreads a warp's scalar stores over the banks (all
+  // 32 for KP = 32; two lanes per bank for KP = 64).
+  static constexpr int CM_SBO = 144, CM_LBO = (2 * KP / 8) * CM_SBO, TBYTES = (R / 4) * CM_LBO;
+  // byte offsets from the 1024-aligned base: G hi / lo, Y hi / lo (the M = 64
+  // read of the last Y lo atom runs up to 8 KB past its start, into TH: rows
+  // that are ignored), the transposed tile hi / lo, the Y G staging rows
+  // (stride QS floats)
   static constexpr int QS = KP + 4;
-  static constexpr int GH = 0, GL = 4096, YH = 8192, YL = 12288, TH = 16384, TL = TH + TBYTES;
+  static constexpr int GH = 0, GL = ATOMS * ATOM_G, YH = 2 * ATOMS * ATOM_G, YL = YH + ATOMS * ATOM_Y;
+  static constexpr int TH = YL + ATOMS * ATOM_Y, TL = TH + TBYTES;
   static constexpr int QO = TL + TBYTES;
   static constexpr int BYTES = QO + R * QS * 4;
   __host__ __device__ static constexpr size_t smem() { return (size_t)BYTES + 1024; }  // + alignment slack
-  static constexpr int TMEM_COLS = 128, D_YG = 0, D_GR = 64;  // TMEM columns of the two accumulators
-  static constexpr uint32_t ID_YG = tc::idesc_tf32(64, 32);
-  static constexpr uint32_t ID_GR = tc::idesc_tf32(64, 64);
-  static_assert(TH >= YL + 4096 && TBYTES >= 4096, "the M = 64 read of Y lo stays inside the allocation");
+  // TMEM: y G (M = 64: the tile's rows in lanes 16 q + r, N = KP) at column 0,
+  // the Gram (M = N = 2 KP) at D_GR
+  static constexpr int TMEM_COLS = KP == 32 ? 128 : 256, D_YG = 0, D_GR = KP == 32 ? 64 : 128;
+  static constexpr uint32_t ID_YG = tc::idesc_tf32(64, KP);
+  static constexpr uint32_t ID_GR = tc::idesc_tf32(2 * KP, 2 * KP);
+  static_assert(YL + (ATOMS - 1) * ATOM_Y + 8 * 1024 <= BYTES, "the M = 64 read of Y lo stays inside the allocation");
+  static_assert(KP == 32 ? (TH == 16384 && TBYTES == 9216) : true, "KP = 32 layout unchanged");
 };
 
 // Per-block resources of the tcgen05 update: the 1024-aligned operand area,
@@ -232,8 +260,12 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
                                                 TcBlock& b) {
   using L = Lay<KP>;
   using U = TcUpd<KP>;
-  static_assert(KP == 32 && L::R == U::R && L::VEC == 4 && L::T == 8, "tile layout of the tcgen05 update");
+  static_assert((KP == 32 || KP == 64) && L::R == U::R && L::VEC == 4 && L::T == KP / 4,
+                "tile layout of the tcgen05 update");
   constexpr int KS = KP / 8;
+  // Gram sums per thread: KP = 32, 8 entries (M = 64 accumulator read as 16
+  // lanes x 16 columns); KP = 64, 32 entries (M = 128: 32 lanes x 32 columns)
+  constexpr int GS = KP == 32 ? 8 : 32;
   uint8_t* sm = b.sm;
   const uint32_t sbase = b.sbase, tmem = b.tmem;
 
@@ -259,9 +291,12 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
   // columns 16 cg + 8 (lane >> 4) + j of that diagonal block.
   const int qd = warp & 3, cg = warp >> 2, gm = qd >> 1;
   const uint32_t t_lanes = (uint32_t)(32 * qd) << 16;
-  float gsum[8];
+  float gsum[GS];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) gsum[j] = 0.f;
+  for (int j = 0; j < GS; ++j) gsum[j] = 0.f;
+  // KP = 64: Gram rows 32-63 of a block against its columns 0-31 lie below the
+  // diagonal, which the fold never reads: those warps skip them
+  const bool gskip = KP == 64 && (qd & 1) && cg == 0;
 
   float tr_hi = 0.f, tr_lo = 0.f, pg_hi = 0.f, pg_lo = 0.f;
   int bad = 0;
@@ -301,14 +336,16 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
       t.y[q] = fmaf(beta, t.pv[q] - qv[q], t.pv[q]);
       t.sy[q] = fmaf(beta, acc[q] - zp[q], acc[q]);
     }
-    split_store4(reinterpret_cast<float*>(sm + U::YH + tc::sw_chunk(team, lt)),
-                 reinterpret_cast<float*>(sm + U::YL + tc::sw_chunk(team, lt)), t.y);
+    const int yo = (lt >> 3) * U::ATOM_Y + tc::sw_chunk(team, lt & 7);
+    split_store4(reinterpret_cast<float*>(sm + U::YH + yo), reinterpret_cast<float*>(sm + U::YL + yo), t.y);
   };
   auto issue_yg = [&]() {
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-      const uint64_t ah = tc::desc_k128(sbase + U::YH + 32 * ks), al = tc::desc_k128(sbase + U::YL + 32 * ks);
-      const uint64_t bh = tc::desc_k128(sbase + U::GH + 32 * ks), bl = tc::desc_k128(sbase + U::GL + 32 * ks);
+      // K step ks: atom ks / 4, 32 bytes (8 TF32) per step inside the atom
+      const int oy = (ks >> 2) * U::ATOM_Y + 32 * (ks & 3), og = (ks >> 2) * U::ATOM_G + 32 * (ks & 3);
+      const uint64_t ah = tc::desc_k128(sbase + U::YH + oy), al = tc::desc_k128(sbase + U::YL + oy);
+      const uint64_t bh = tc::desc_k128(sbase + U::GH + og), bl = tc::desc_k128(sbase + U::GL + og);
       tc::mma(tmem + U::D_YG, al, bh, U::ID_YG, ks > 0);
       tc::mma(tmem + U::D_YG, ah, bl, U::ID_YG, 1);
       tc::mma(tmem + U::D_YG, ah, bh, U::ID_YG, 1);
@@ -328,6 +365,27 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
     tc::commit(b.bar_gr);
   };
 
+  // this tile's Gram into the float sums (round-to-nearest adds).  KP = 32:
+  // M = 64 accumulator, Gram row 16 (qd & 1) + (lane & 15) of matrix gm in
+  // lane 32 qd + (lane & 15), columns 16 cg + 8 (lane >> 4) + j of its diagonal
+  // block; KP = 64: M = 128, Gram row 32 (qd & 1) + lane of matrix gm in lane
+  // 32 qd + lane, columns 32 cg + j of its diagonal block
+  auto gram_read = [&]() {
+    if constexpr (KP == 32) {
+      float g[8];
+      tc::ld16x16(tmem + t_lanes + U::D_GR + 32 * gm + 16 * cg, g);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) gsum[j] += g[j];
+    } else {
+      if (!gskip) {
+        float g[32];
+        tc::ld32x32(tmem + t_lanes + U::D_GR + KP * gm + 32 * cg, g);
+#pragma unroll
+        for (int j = 0; j < GS; ++j) gsum[j] += g[j];
+      }
+    }
+  };
+
   if (tid == 0) b.tmo_flag[1] = ((const volatile FistaState*)st)->hooks;  // read by tid 0 only
   TcRow cur;
   if (ntiles > 0) {
@@ -338,8 +396,8 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
       const int n = e / (KP / 4), c = e % (KP / 4);
       float v[4];
       load_row<4>(a.Gy + n * KP + 4 * c, v);
-      split_store4(reinterpret_cast<float*>(sm + U::GH + tc::sw_chunk(n, c)),
-                   reinterpret_cast<float*>(sm + U::GL + tc::sw_chunk(n, c)), v);
+      const int go = (c >> 3) * U::ATOM_G + tc::sw_chunk(n, c & 7);
+      split_store4(reinterpret_cast<float*>(sm + U::GH + go), reinterpret_cast<float*>(sm + U::GL + go), v);
     }
     load_tile(0, cur);
     tc::fence_smem_to_async();
@@ -364,12 +422,18 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
     }
     // y G of this tile -> staging rows
     wait_bar(b.bar_yg, ph0 + it);
-    if (qd < 2 && !dead) {
-      float v[8];
-      tc::ld16x16(tmem + t_lanes + U::D_YG + 16 * cg, v);
-      float* qo = reinterpret_cast<float*>(sm + U::QO) + (16 * qd + (lane & 15)) * U::QS + 16 * cg + 8 * (lane >> 4);
-      *reinterpret_cast<float4*>(qo) = make_float4(v[0], v[1], v[2], v[3]);
-      *reinterpret_cast<float4*>(qo + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    // the tile's R rows sit in lane quarters 0 .. R/16 - 1; the two warps of a
+    // quarter take KP / 2 columns each, 16 per load
+    if (qd < U::R / 16 && !dead) {
+#pragma unroll
+      for (int i = 0; i < KP / 32; ++i) {
+        float v[8];
+        tc::ld16x16(tmem + t_lanes + U::D_YG + (KP / 2) * cg + 16 * i, v);
+        float* qo = reinterpret_cast<float*>(sm + U::QO) + (16 * qd + (lane & 15)) * U::QS + (KP / 2) * cg + 16 * i +
+                    8 * (lane >> 4);
+        *reinterpret_cast<float4*>(qo) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(qo + 4) = make_float4(v[4], v[5], v[6], v[7]);
+      }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -397,15 +461,10 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
     // back before this tile's transposed rows overwrite the operand
     if (it > 0) {
       wait_bar(b.bar_gr, ph0 + it - 1);
-      if (!dead) {
-        float g[8];
-        tc::ld16x16(tmem + t_lanes + U::D_GR + 32 * gm + 16 * cg, g);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) gsum[j] += g[j];
-      }
+      if (!dead) gram_read();
     }
-    // transposed tile: Xbar^n in feature rows 0..31, Y^{n+1} = xbar^n +
-    // beta_{n+1} (xbar^n - xbar^{n-1}) in 32..63 (4 core-matrix groups further)
+    // transposed tile: Xbar^n in feature rows 0..KP-1, Y^{n+1} = xbar^n +
+    // beta_{n+1} (xbar^n - xbar^{n-1}) in KP..2KP-1 (KP / 8 core-matrix groups further)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float xv = cur.active ? x[q] : 0.f;
@@ -417,8 +476,8 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
       const int o = (m >> 3) * U::CM_SBO + (team >> 2) * U::CM_LBO + (m & 7) * 16 + (team & 3) * 4;
       *reinterpret_cast<uint32_t*>(sm + U::TH + o) = hx;
       *reinterpret_cast<uint32_t*>(sm + U::TL + o) = lx;
-      *reinterpret_cast<uint32_t*>(sm + U::TH + o + 4 * U::CM_SBO) = hy;
-      *reinterpret_cast<uint32_t*>(sm + U::TL + o + 4 * U::CM_SBO) = ly;
+      *reinterpret_cast<uint32_t*>(sm + U::TH + o + (KP / 8) * U::CM_SBO) = hy;
+      *reinterpret_cast<uint32_t*>(sm + U::TL + o + (KP / 8) * U::CM_SBO) = ly;
     }
     // the next tile's rows (its Y G operand is free: this tile's Y G completed)
     const bool more = it + 1 < ntiles;
@@ -436,12 +495,7 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
   }
   if (ntiles > 0) {
     wait_bar(b.bar_gr, ph0 + ntiles - 1);
-    if (!dead) {
-      float g[8];
-      tc::ld16x16(tmem + t_lanes + U::D_GR + 32 * gm + 16 * cg, g);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) gsum[j] += g[j];
-    }
+    if (!dead) gram_read();
   }
   b.tiles = ph0 + ntiles;
   b.dead = dead;
@@ -475,10 +529,18 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
     a.sc_part[slot * 4 + 2] = bd;
     a.sc_part[slot * 4 + 3] = w;  // warps whose wait gave up (fold: CLUSTER_ETIMEOUT)
   }
-  float* go = a.gram_part + (size_t)slot * 2 * L::E2 + gm * L::E2 + (16 * (qd & 1) + (lane & 15)) * KP + 16 * cg +
-              8 * (lane >> 4);
-  *reinterpret_cast<float4*>(go) = make_float4(gsum[0], gsum[1], gsum[2], gsum[3]);
-  *reinterpret_cast<float4*>(go + 4) = make_float4(gsum[4], gsum[5], gsum[6], gsum[7]);
+  if constexpr (KP == 32) {
+    float* go = a.gram_part + (size_t)slot * 2 * L::E2 + gm * L::E2 + (16 * (qd & 1) + (lane & 15)) * KP + 16 * cg +
+                8 * (lane >> 4);
+    *reinterpret_cast<float4*>(go) = make_float4(gsum[0], gsum[1], gsum[2], gsum[3]);
+    *reinterpret_cast<float4*>(go + 4) = make_float4(gsum[4], gsum[5], gsum[6], gsum[7]);
+  } else if (!gskip) {
+    // (skipped: below the diagonal, never read by the fold)
+    float* go = a.gram_part + (size_t)slot * 2 * L::E2 + gm * L::E2 + (32 * (qd & 1) + lane) * KP + 32 * cg;
+#pragma unroll
+    for (int j = 0; j < GS; j += 4)
+      *reinterpret_cast<float4*>(go + j) = make_float4(gsum[j], gsum[j + 1], gsum[j + 2], gsum[j + 3]);
+  }
   // the staging rows (dred) are written again only after the next range's
   // first barrier, which every thread reaches after tid 0 has read them
 }

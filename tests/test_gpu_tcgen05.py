@@ -1,5 +1,5 @@
 """The row-local update on the fifth-generation tensor cores (tcgen05.mma,
-accumulators in tensor memory; k in 17..32) against the warp-level mma.sync
+accumulators in tensor memory; k in 17..64) against the warp-level mma.sync
 update: both compute the same 3xTF32 products in the same order, so every bit
 of the iterates, losses and norms agrees.  Also the bounded-wait path: a wait
 that gives up ends the run with CLUSTER_ETIMEOUT and leaves the context usable."""
@@ -55,18 +55,21 @@ def test_tcgen05_update_equals_warp_update_bitwise(k, precision):
 def test_tcgen05_update_in_a_batch_equals_solo():
     specs = [synth.GraphSpec("dcsbm", 9001, 32, 81, mean_deg=20.0),
              synth.GraphSpec("dcsbm", 4000, 20, 82, mean_deg=30.0),
-             synth.GraphSpec("dcsbm", 700, 8, 83, mean_deg=12.0)]
+             synth.GraphSpec("dcsbm", 700, 8, 83, mean_deg=12.0),
+             synth.GraphSpec("dcsbm", 3000, 50, 84, mean_deg=15.0)]
     inst = []
     for sp in specs:
         rp, c, v = synth.make_graph(sp)
         U0 = synth.dirichlet_u0(sp.n, sp.k, sp.seed)
         inst.append(tuple(t.cuda().contiguous() for t in (rp, c, v, U0)))
-    for eng in (0, 1):
-        b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=20, update_engine=eng)
+    # batch engine, solo engine: tcgen05 (k <= 32) vs warp, warp vs tcgen05,
+    # tcgen05 for every k in 17..64 vs warp
+    for eng_b, eng_s in ((0, 1), (1, 0), (2, 1)):
+        b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=20, update_engine=eng_b)
         b.step(20)
         for i, (rp, c, v, U0) in enumerate(inst):
-            U, _ = _run(rp, c, v, U0, 20, update_engine=1 - eng)   # the other engine, alone
-            assert torch.equal(b.get_U(i), U), (eng, i)
+            U, _ = _run(rp, c, v, U0, 20, update_engine=eng_s)
+            assert torch.equal(b.get_U(i), U), (eng_b, i)
         b.close()
 
 
@@ -131,3 +134,52 @@ def test_tcgen05_update_with_a_stop_rule_inside_a_graph():
     assert rt["done"] == rw["done"] == 1 and rt["status"] == rw["status"] == pkg.OK
     assert rt["out_iter"] == rw["out_iter"] < 400
     assert torch.equal(Ut, Uw)
+
+
+# ---- k in 33..64 (KP = 64): y G as M = 64, N = K = 64 with two swizzle atoms
+# per row; the Gram as M = N = 128 over [Xbar | Y] ----
+@pytest.mark.parametrize("k", [33, 48, 64])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tcgen05_k64_update_equals_warp_update_bitwise(k, precision):
+    spec = synth.GraphSpec("dcsbm", 20011, k, 90 + k, mean_deg=25.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, k, 90 + k, device="cuda")
+    Ut, rt = _run(rp, c, v, U0, 25, precision=precision, update_engine=2)
+    Uw, rw = _run(rp, c, v, U0, 25, precision=precision, update_engine=1)
+    assert rt["iters"] == rw["iters"] == 25
+    assert torch.equal(Ut, Uw)
+    assert rt["f"] == rw["f"] and rt["pg_norm"] == rw["pg_norm"] and rt["trace_SU"] == rw["trace_SU"]
+    if precision == 0:
+        S = to_scipy(rp, c, v, spec.n)
+        o = oracle.fista(S, U0.cpu().numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=25,
+                         stop="none")
+        assert maxabs(Ut.cpu().numpy(), o.U) <= 1e-5
+
+
+# one partial tile of 16 rows (n = 5), one row past a tile (17), a few tiles
+@pytest.mark.parametrize("n", [5, 17, 100, 1000])
+def test_tcgen05_k64_update_small_and_ragged_n(n):
+    spec = synth.GraphSpec("dcsbm", n, 64, 600 + n, mean_deg=min(12.0, n / 2.0))
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(n, 64, 600 + n, device="cuda")
+    Ut, rt = _run(rp, c, v, U0, 30, update_engine=2)
+    S = to_scipy(rp, c, v, n)
+    o = oracle.fista(S, U0.cpu().numpy().astype(np.float64), 1.0 / oracle.lipschitz(S), max_iter=30, stop="none")
+    assert maxabs(Ut.cpu().numpy(), o.U) <= 1e-5
+    s2 = float((v.double() ** 2).sum())
+    assert abs(rt["f"] - o.losses[rt["f_iter"]]) <= 1e-6 * max(abs(o.losses[rt["f_iter"]]), s2)
+
+
+def test_tcgen05_k64_wait_that_gives_up_is_a_status():
+    spec = synth.GraphSpec("dcsbm", 3000, 64, 95, mean_deg=20.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(spec.n, 64, 95, device="cuda")
+    s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50, update_engine=2)
+    s.step(2)
+    U2 = s.get_U().clone()
+    s.test_hooks(1)
+    rep = s.step(4)
+    assert rep["status"] == pkg.ETIMEOUT and rep["done"] == 1 and rep["out_iter"] == 2
+    assert torch.equal(s.get_U(), U2)
+    s.test_hooks(0)
+    s.close()
