@@ -24,10 +24,12 @@
 //     the compute warps).
 //   * y G(Y): kind::tf32, 3xTF32 (hi/lo split), M = 128 = the tile's rows, so
 //     row r of the accumulator is TMEM lane r and each thread reads its own
-//     row back (tcgen05.ld 32x32b).  The y operand (hi, lo) goes to the
-//     Gram operand's area (free again once the previous tile's Gram has
-//     completed), so the whole input stage is free as soon as the warpgroup
-//     has read its rows: the next tile's loads overlap y G and the projection.
+//     row back (tcgen05.ld 32x32b).  Each thread writes its row of the y
+//     operand (hi, lo) over its own rows of the stage's xbar^{n-2} and
+//     xbar^{n-1} tiles, just read: the next tile's z tiles load as soon as the
+//     warpgroup has read its rows, its xbar tiles once y G has completed, and
+//     the previous tile's Gram is read back while y G runs, so neither
+//     tensor-core round trip of a tile waits on the other.
 //   * Gram of [Xbar^n | Y^{n+1}] (64 features): kind::f16 with both operands
 //     MN-major, i.e. the row-major tile itself (no transpose).  Each value is
 //     scaled by 2^13 and split into two float16 parts h + l (h = s x rounded
@@ -236,10 +238,13 @@ struct StreamCta {
 
 // The helper thread of warpgroup w, in the warpgroup's order: the first
 // tile's loads; then per tile, once the warpgroup has read its rows and
-// written its y operand (y-ready): the next tile's loads into the freed stage
-// and y G; once it has written the Gram operand (G-ready): the Gram.  Every
-// wait is bounded and also ends on the abort flag.  Returns after its issued
-// loads have landed and its MMAs have completed (each bounded).
+// written its y operand over the stage's xbar^{n-1} and xbar^{n-2} tiles
+// (y-ready): the next tile's z and z^{prev} tiles into the freed slots and
+// y G; once y G has completed: the next tile's xbar^{n-1} and xbar^{n-2}
+// tiles over the y operand; once the warpgroup has written the Gram operand
+// (G-ready): the Gram.  Every wait is bounded and also ends on the abort flag.
+// Returns after its MMAs have completed and its issued loads have landed
+// (each bounded).
 __device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMaps& m, int64_t pass, int w) {
   const CUtensorMap* mz = &m.Z[(pass + 1) & 1];   // S Xbar^{pass}
   const CUtensorMap* mp = &m.X[pass & 1];         // Xbar^{pass}
@@ -253,13 +258,17 @@ __device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMa
   const int ntw = (c.cnt + 1 - w) / 2;
   const uint32_t st = c.sb + OFF_WG + (uint32_t)w * WG_B;
   const uint32_t full = c.bar(w, BAR_FULL);
-  auto load = [&](int jj) {
-    const int row = (int)((c.t0 + 2 * jj + w) * R);
+  auto tile_row = [&](int jj) { return (int)((c.t0 + 2 * jj + w) * R); };
+  // slots 0 and 3 (z, z^{prev}); the stage's whole byte count is expected here
+  auto load_z = [&](int jj) {
     expect_tx(full, STAGE_B);
-    tma_load_2d(st + 0 * TILE_B, mz, 0, row, full);
-    tma_load_2d(st + 1 * TILE_B, mp, 0, row, full);
-    tma_load_2d(st + 2 * TILE_B, mq, 0, row, full);
-    tma_load_2d(st + 3 * TILE_B, mzp, 0, row, full);
+    tma_load_2d(st + 0 * TILE_B, mz, 0, tile_row(jj), full);
+    tma_load_2d(st + 3 * TILE_B, mzp, 0, tile_row(jj), full);
+  };
+  // slots 1 and 2 (xbar^{n-1}, xbar^{n-2})
+  auto load_x = [&](int jj) {
+    tma_load_2d(st + 1 * TILE_B, mp, 0, tile_row(jj), full);
+    tma_load_2d(st + 2 * TILE_B, mq, 0, tile_row(jj), full);
   };
   auto wait = [&](uint32_t bar, uint32_t par) -> bool {
     for (uint32_t i = 0; i < tc::kWaitPolls; ++i) {
@@ -269,31 +278,39 @@ __device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMa
     *reinterpret_cast<volatile int*>(c.flags) = 1;
     return false;
   };
-  int nl = 0;
+  int nl = 0;          // tiles whose loads were (at least in part) issued
+  bool half = false;   // the last of them still lacks its x tiles
   if (ntw > 0) {
-    load(0);
+    load_z(0);
+    load_x(0);
     nl = 1;
   }
   for (int jj = 0; jj < ntw; ++jj) {
     if (!wait(c.bar(w, BAR_YREADY), (uint32_t)jj & 1u)) break;
     if (jj + 1 < ntw) {
-      load(jj + 1);
+      load_z(jj + 1);
       ++nl;
+      half = true;
     }
-    // y G(Y): A = y hi / lo (in the Gram operand's area), B = G(Y) hi / lo
+    // y G(Y): A = y hi / lo (stage slots 2 / 1), B = G(Y) hi / lo
     tc::fence_after_sync();
     {
       const uint32_t d = c.tmem + (uint32_t)(w * COL_WG + COL_YG);
-      const uint32_t ya = st + STAGE_B;
+      const uint32_t yh = st + 2 * TILE_B, yl = st + 1 * TILE_B;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t ah = tc::desc_k128(ya + 32 * ks), al = tc::desc_k128(ya + TILE_B + 32 * ks);
+        const uint64_t ah = tc::desc_k128(yh + 32 * ks), al = tc::desc_k128(yl + 32 * ks);
         const uint64_t bh = tc::desc_k128(c.sb + OFF_GH + 32 * ks), bl = tc::desc_k128(c.sb + OFF_GL + 32 * ks);
         tc::mma(d, al, bh, idesc_tf32_m128(), ks > 0);
         tc::mma(d, ah, bl, idesc_tf32_m128(), 1);
         tc::mma(d, ah, bh, idesc_tf32_m128(), 1);
       }
       if (!hook) tc::commit(c.bar(w, BAR_YGDONE));
+    }
+    if (half) {
+      if (!wait(c.bar(w, BAR_YGDONE), (uint32_t)jj & 1u)) break;
+      load_x(jj + 1);
+      half = false;
     }
     if (!wait(c.bar(w, BAR_GREADY), (uint32_t)jj & 1u)) break;
     // Gram of [Xbar^n | Y^{n+1}] over the tile's rows (K = 128, 8 steps of 16):
@@ -318,10 +335,13 @@ __device__ __forceinline__ void stream_helper(const StreamCta& c, const StreamMa
       tc::commit(c.bar(w, BAR_GRDONE));
     }
   }
-  // nothing of this thread may be in flight when the CTA exits
+  // nothing of this thread may be in flight when the CTA exits: its MMAs
+  // first (they may still read the y operand), then the rest of a half-issued
+  // stage, so that the stage's phase can complete, then the loads
   const uint32_t fin = c.bars + 8u * (uint32_t)(10 + w);
   tc::commit(fin);
   tc::bar_wait(fin, 0);
+  if (half) load_x(nl - 1);
   if (nl > 0) tc::bar_wait(full, (uint32_t)(nl - 1) & 1u);
 }
 
@@ -417,12 +437,6 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     const int64_t row = (c.t0 + 2 * jj + w) * R + t;
     const bool active = row < a.n;
     if (!wait(c.bar(w, BAR_FULL), (uint32_t)jj & 1u)) break;
-    // the Gram operand's area takes this tile's y operand once the previous
-    // tile's Gram has completed
-    if (jj > 0) {
-      if (!wait(c.bar(w, BAR_GRDONE), (uint32_t)(jj - 1) & 1u)) break;
-      gram_back();
-    }
     float y[32], sy[32], pv[32];
     float dq[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums: short dependency chains
 #pragma unroll
@@ -442,8 +456,10 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
         y[f] = fmaf(beta, pvv[q] - qv[q], pvv[q]);
         sy[f] = fmaf(beta, zv[q] - zp[q], zv[q]);
       }
-      // y operand (row t, 128-byte swizzle, K-major): hi, lo
-      split11_store4(reinterpret_cast<float*>(gp + off), reinterpret_cast<float*>(gp + TILE_B + off), &y[4 * ch]);
+      // y operand (row t, 128-byte swizzle, K-major) over the row's chunk of
+      // xbar^{n-2} (hi) and xbar^{n-1} (lo), both just read into y
+      split11_store4(reinterpret_cast<float*>(stp + 2 * TILE_B + off), reinterpret_cast<float*>(stp + 1 * TILE_B + off),
+                     &y[4 * ch]);
     }
     {
       uint32_t pu[32];
@@ -457,6 +473,12 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     arrive(c.bar(w, BAR_YREADY));
+    // while y G runs: the previous tile's Gram into the float pairs (which
+    // also frees the Gram operand's area for this tile)
+    if (jj > 0) {
+      if (!wait(c.bar(w, BAR_GRDONE), (uint32_t)(jj - 1) & 1u)) break;
+      gram_back();
+    }
     if (!wait(c.bar(w, BAR_YGDONE), (uint32_t)jj & 1u)) break;
 
     float v[32];
@@ -532,8 +554,8 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
         }
       }
     }
-    // the y operand has been read (y G completed): s [xbar^n | y^{n+1}] as
-    // float16 h + l over it, row t, chunk ch = features 8 ch ..
+    // the Gram operand's area (the previous tile's Gram has completed):
+    // s [xbar^n | y^{n+1}] as float16 h + l, row t, chunk ch = features 8 ch ..
     wait_ld();
     pin32(pvu);
 #pragma unroll
