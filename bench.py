@@ -9,7 +9,10 @@ step is one fused iteration of the solver.  Both arithmetic forms run on the
 same graph and start point: plain FP32 and mixed (bfloat16 gathers and S
 values, FP32 accumulation, FP64 scalars).  ``value`` is the mixed form's
 iterations/s; the FP32 form's rate and the objectives of both after the same
-number of iterations are reported beside it.
+number of iterations are reported beside it.  The same run (single GPU) also
+measures the batched form (512 uneven instances, key ``batch``) and the
+served form (a Poisson stream at a load the server sustains, key ``serve``);
+``--extras ""`` skips them.
 
 Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1 under
 torch.distributed.run every rank solves its own instance (replicas, weak
@@ -34,7 +37,7 @@ if ROOT not in sys.path:
 
 METRIC = "PG iters/s, mixed vs FP32, at equal objective (n=70M,k=32); serving p99 latency"
 UNIT = "iter/s"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k32_n70M.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k32_n8M.json")
 SPMM_SRC = [os.path.join(ROOT, "paper_2506_04045_b300", "csrc", f)
             for f in ("iter_common.cuh", "spmm_kernels.cuh", "state.h", "schedule.cuh", "init_kernels.cuh",
                       "solver.cu")]
@@ -62,6 +65,14 @@ def parse():
     p.add_argument("--serve-tol", type=float, default=1e-5)
     p.add_argument("--tick", type=int, default=16)
     p.add_argument("--instances", type=int, default=512)
+    p.add_argument("--extras", default="batch,serve",
+                   help="paper workload: also measure these forms in the same run (single GPU): batch "
+                        "(the 512-instance batch, --extra-steps timed iterations), serve (a Poisson stream at "
+                        "--extra-serve-rate); empty to skip")
+    p.add_argument("--extra-steps", type=int, default=10)
+    p.add_argument("--extra-serve-rate", type=float, default=0.5)
+    p.add_argument("--extra-serve-duration", type=float, default=20.0)
+    p.add_argument("--extra-serve-drain", type=float, default=25.0)
     p.add_argument("--n", type=int, default=70_000_000)
     p.add_argument("--k", type=int, default=32)
     p.add_argument("--mean-deg", type=float, default=28.9)
@@ -234,18 +245,40 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(form: str, workload: str):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu capture,
-    or None when the capture is of another workload or an older kernel source."""
+def traffic_capture():
+    """The committed ncu capture of DRAM bytes per launch (a smaller case of the
+    same generator), or None when it was taken with older kernel sources."""
     try:
         with open(TRAFFIC_FILE) as fh:
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("kernel_sha") != kernel_digest() or d.get("workload") != workload:
+    return d if d.get("kernel_sha") == kernel_digest() else None
+
+
+def traffic_for(form: str, workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed capture
+    when it is of this very workload and the current sources, else None."""
+    d = traffic_capture()
+    if d is None or d.get("workload") != workload:
         return None
     ent = d.get(form)
     return None if ent is None else ent.get("bytes_per_launch")
+
+
+def traffic_small_case(form: str):
+    """The committed capture's figures for `form` when its sources are current:
+    bytes and algorithmic bytes per launch of the gather and the update at the
+    capture's (smaller) size, not scaled (see the capture's note)."""
+    d = traffic_capture()
+    if d is None or form not in d:
+        return None
+    e = d[form]
+    return {"workload": d["workload"], "kernel": e["kernel"], "bytes_per_launch": e["bytes_per_launch"],
+            "alg_bytes_per_launch": e["alg_bytes_per_launch"],
+            "traffic_over_alg": e["bytes_per_launch"] / e["alg_bytes_per_launch"],
+            "update_kernel": e.get("update_kernel"), "update_bytes_per_launch": e.get("update_bytes_per_launch"),
+            "note": d.get("note")}
 
 
 # ---------------------------------------------------------------------------
@@ -482,7 +515,8 @@ def run_native(args, ws, rank, local):
     traffic = traffic_for(head + ("_fused" if args.fused else ""),
                           f"dcsbm n={n} k={k} nnz={nnz} seed={args.seed}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
+            "traffic": traffic, "traffic_small_case": None if args.fused else traffic_small_case(head),
+            "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": b_pass,
             "pass_ms": kt["pass_ms"], "heavy_ms": kt["heavy_ms"], "update_ms": kt["update_ms"],
             "fold_ms": kt["fold_ms"], "iteration_alg_bytes": b_iter,
             "iteration_frac": b_iter / (r["ms_total"] / K / 1000.0) / 1e9 / hbm}
@@ -515,6 +549,31 @@ def run_native(args, ws, rank, local):
         except Exception as exc:
             tto = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
+    # the batched and served forms, measured in the same run (single GPU only)
+    extras = {}
+    wanted = [x for x in args.extras.split(",") if x]
+    if ws == 1 and wanted:
+        del rp, col, val, U0
+        torch.cuda.empty_cache()
+        if "batch" in wanted:
+            try:
+                bres, bwork = batch_measure(args, ranks, rank, args.extra_steps, max(3, W), forms)
+                bh = "mixed" if "mixed" in bres else forms[0]
+                extras["batch"] = {"metric": "instance-iterations/s", "value": bres[bh]["inst_it_s"],
+                                   "steps": args.extra_steps, "warmup": max(3, W), "config": bwork,
+                                   "iteration_frac": bres[bh]["bytes_iter"] / (bres[bh]["ms"] / args.extra_steps
+                                                                             / 1000.0) / 1e9 / hbm,
+                                   "forms": batch_forms_summary(bres, args.extra_steps, compact=True)}
+            except Exception as exc:
+                extras["batch"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        if "serve" in wanted:
+            try:
+                extras["serve"] = serve_measure(args, rank, args.extra_serve_rate, args.extra_serve_duration,
+                                                args.extra_serve_drain)
+                extras["serve"]["requests"] = extras["serve"]["requests"][:40]
+            except Exception as exc:
+                extras["serve"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+
     # r["ms_total"] is already the slowest rank's time: whole-job iterations / that time
     _, value = ranks.weak_throughput(K, r["ms_total"] / 1000.0)
     eq = None
@@ -543,6 +602,7 @@ def run_native(args, ws, rank, local):
         "mixed_over_fp32": (res["mixed"]["it_s"] / res["fp32"]["it_s"]) if eq is not None else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": r["launches"],
+        "batch": extras.get("batch"), "serve": extras.get("serve"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -662,22 +722,17 @@ def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
             "note": "one solve: H2D of S and U0, cluster_init, K iterations each reading the loss, D2H of U"}
 
 
-def run_batch(args, ws, rank, local):
-    """Batched workload: independent instances with n log-uniform in [500, 2e5],
-    k uniform in {4, 8, 16, 32, 64}, mean degree uniform in [10, 40], advanced
-    together by the segmented launches; a step is one iteration of every
-    instance.  value = instance-iterations/s."""
+def batch_measure(args, ranks, rank, K, W, forms):
+    """Generate the batched workload (--instances instances, seed 3 + 1000 rank)
+    and time K batched iterations of each form after autotuning and W warm-up
+    iterations.  Returns the per-form results and the workload description."""
     import torch
 
     import synth
     import paper_2506_04045_b300 as pkg
-    torch.cuda.set_device(local)
-    ranks = Ranks(ws)
-    pkg.load()
     specs = synth.batch_specs(args.instances, seed=3 + 1000 * rank)
     t0 = time.perf_counter()
-    inst, nnz_tot, n_tot, b_iter = [], 0, 0, 0.0
-    forms = [f for f in args.forms.split(",") if f]
+    inst, nnz_tot, n_tot = [], 0, 0
     for sp in specs:
         rp, c, v = synth.make_graph(sp, device="cuda")
         U0 = synth.dirichlet_u0(sp.n, sp.k, sp.seed, device="cuda")
@@ -686,15 +741,14 @@ def run_batch(args, ws, rank, local):
         n_tot += sp.n
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    hbm, peak_kind = peaks()
-    K, W = args.steps, args.warmup
     stream = torch.cuda.current_stream()
     res = {}
     for form in forms:
         mixed = form == "mixed"
         t1 = time.perf_counter()
         b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
-                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
+                      precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel,
+                      update_engine=args.update_engine, overlap=args.overlap)
         init_s = time.perf_counter() - t1
         desc = b.autotune(trials=1)
         b.step(W)
@@ -716,6 +770,46 @@ def run_batch(args, ws, rank, local):
                      "bytes_iter": bytes_iter, "clocks": cs.summary(),
                      "iters_min": min(r["iters"] for r in reps), "iters_max": max(r["iters"] for r in reps)}
         b.close()
+    del inst
+    torch.cuda.empty_cache()
+    workload = {"workload": f"{len(specs)} DC-SBM instances, n log-uniform [500, 2e5], k in {{4..64}}, "
+                            f"mean degree U[10,40]; sum n = {n_tot:,}, sum nnz = {nnz_tot:,}",
+                "instances": len(specs), "sum_n": n_tot, "sum_nnz": nnz_tot, "gen_seconds": round(gen_s, 1),
+                "l2": "working set larger than L2; no flush"}
+    return res, workload
+
+
+def batch_forms_summary(res, K, compact=False):
+    out = {}
+    for f, v in res.items():
+        d = {"inst_it_s": v["inst_it_s"], "ms_per_step": v["ms"] / K, "init_s": round(v["init_s"], 2),
+             "model_GBps": v["bytes_iter"] * K / (v["ms"] / 1000.0) / 1e9, "clocks": v["clocks"],
+             "iters_done": [v["iters_min"], v["iters_max"]]}
+        if compact:
+            d["classes"] = [{key: c.get(key) for key in ("kp", "instances", "gather_ms", "update_ms",
+                                                        "gather_nonzeros_per_batch", "gather_rows_per_unit")}
+                            for c in v["desc"]["classes"]]
+        else:
+            d["classes"] = v["desc"]["classes"]
+        out[f] = d
+    return out
+
+
+def run_batch(args, ws, rank, local):
+    """Batched workload: independent instances with n log-uniform in [500, 2e5],
+    k uniform in {4, 8, 16, 32, 64}, mean degree uniform in [10, 40], advanced
+    together by the segmented launches; a step is one iteration of every
+    instance.  value = instance-iterations/s."""
+    import torch
+
+    import paper_2506_04045_b300 as pkg
+    torch.cuda.set_device(local)
+    ranks = Ranks(ws)
+    pkg.load()
+    hbm, peak_kind = peaks()
+    K, W = args.steps, args.warmup
+    forms = [f for f in args.forms.split(",") if f]
+    res, workload = batch_measure(args, ranks, rank, K, W, forms)
     head = "mixed" if "mixed" in res else forms[0]
     r = res[head]
     achieved = r["bytes_iter"] * K / (r["ms"] / 1000.0) / 1e9
@@ -723,14 +817,8 @@ def run_batch(args, ws, rank, local):
             "unit": "instance-iter/s", "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": r["ms"] / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32" if head == "mixed" else "f32", "data": "synthetic",
-            "config": {"workload": f"{len(inst)} DC-SBM instances, n log-uniform [500, 2e5], k in {{4..64}}, "
-                                   f"mean degree U[10,40]; sum n = {n_tot:,}, sum nnz = {nnz_tot:,}",
-                       "instances": len(inst), "sum_n": n_tot, "sum_nnz": nnz_tot, "gen_seconds": round(gen_s, 1),
-                       "l2": "working set larger than L2; no flush"},
-            "forms": {f: {"inst_it_s": v["inst_it_s"], "ms_per_step": v["ms"] / K, "init_s": round(v["init_s"], 2),
-                          "model_GBps": v["bytes_iter"] * K / (v["ms"] / 1000.0) / 1e9, "classes": v["desc"]["classes"],
-                          "clocks": v["clocks"], "iters_done": [v["iters_min"], v["iters_max"]]}
-                      for f, v in res.items()},
+            "config": workload,
+            "forms": batch_forms_summary(res, K),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "whole batched iteration (all classes)", "peak_kind": peak_kind},
             "clocks": r["clocks"]}
@@ -824,14 +912,14 @@ def run_er2(args, ws, rank, local):
     ranks.close()
 
 
-def run_serve(args, ws, rank, local):
-    """Serving workload: Poisson arrivals (rate --rate) of solves with n
-    log-uniform in [1e3, 2e6], k in {8, 16, 32, 64, 128}, mean degree U[10, 40],
-    each run to PG_REL --serve-tol (cap --serve-max-iter), admitted under a
-    --budget-gb device budget.  Requests are drawn from a pool of --pool
-    pre-generated graphs (host arrays).  Reports latency percentiles of the
-    requests that finished, and offered vs achieved load; requests still
-    pending at the end are counted, not dropped."""
+def serve_measure(args, rank, rate, duration, drain):
+    """Poisson arrivals at `rate` per second for `duration` seconds of solves
+    drawn from a pool of --pool pre-generated graphs (n log-uniform in
+    [1e3, 2e6], k in {8, 16, 32, 64, 128}, mean degree U[10, 40]; host
+    arrays), each run to PG_REL --serve-tol (cap --serve-max-iter) under a
+    --budget-gb device budget; completions are awaited `drain` seconds more.
+    Returns latency percentiles of the finished requests, offered vs achieved
+    load and the requests still pending (counted, not dropped)."""
     import random
     import threading
 
@@ -840,8 +928,6 @@ def run_serve(args, ws, rank, local):
 
     import synth
     import paper_2506_04045_b300 as pkg
-    torch.cuda.set_device(local)
-    pkg.load()
     specs = synth.batch_specs(args.pool, seed=4 + 1000 * rank, n_range=(1_000, 2_000_000),
                               ks=(8, 16, 32, 64, 128))
     pool = []
@@ -851,8 +937,8 @@ def run_serve(args, ws, rank, local):
         pool.append((rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), U0.cpu().numpy()))
         del rp, c, v, U0
     torch.cuda.empty_cache()
-    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap,
-                     stop_rule=pkg.STOP_PG_REL,
+    srv = pkg.Server(hbm_budget=int(args.budget_gb * (1 << 30)), iters_per_tick=args.tick, relabel=args.relabel,
+                     update_engine=args.update_engine, overlap=args.overlap, stop_rule=pkg.STOP_PG_REL,
                      tol=args.serve_tol, max_iter=args.serve_max_iter, borrow_host=True)
     rng = random.Random(4 + rank)
     tickets, submit_t, which = [], {}, {}
@@ -872,8 +958,8 @@ def run_serve(args, ws, rank, local):
         t_start = time.perf_counter()
         t_next = t_start
         while True:
-            t_next += rng.expovariate(args.rate)
-            if t_next - t_start > args.duration:
+            t_next += rng.expovariate(rate)
+            if t_next - t_start > duration:
                 break
             delay = t_next - time.perf_counter()
             if delay > 0:
@@ -885,7 +971,7 @@ def run_serve(args, ws, rank, local):
             which[tk] = pi
         t_arrivals_end = time.perf_counter()
         results = {}
-        deadline = t_arrivals_end + args.drain
+        deadline = t_arrivals_end + drain
         while time.perf_counter() < deadline and len(results) < len(tickets):
             for tk in tickets:
                 if tk in results:
@@ -907,23 +993,36 @@ def run_serve(args, ws, rank, local):
     lat = np.array([r[1]["total_s"] for r in ok]) if ok else np.array([])
     pending = len(tickets) - len(results)
     span = t_end - t_start
-    line = {"metric": "serving p99 latency (continuous batching)", "value": float(np.percentile(lat, 99)) if ok else None,
-            "unit": "s", "n_gpus": ws, "steps": len(tickets), "warmup": 0, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"Poisson {args.rate}/s for {args.duration}s, n log-uniform [1e3, 2e6], "
+    return {"config": {"workload": f"Poisson {rate}/s for {duration}s, n log-uniform [1e3, 2e6], "
                                    f"k in {{8..128}}, mean degree U[10,40], PG_REL {args.serve_tol}, "
                                    f"max_iter {args.serve_max_iter}, budget {args.budget_gb} GB, pool {args.pool}",
-                       "tick": args.tick},
+                       "tick": args.tick, "drain_s": drain},
+            "requests_submitted": len(tickets),
             "p50_s": float(np.percentile(lat, 50)) if ok else None,
             "p99_s": float(np.percentile(lat, 99)) if ok else None,
             "completed": len(ok), "failed": len(results) - len(ok), "pending_at_end": pending,
-            "offered_rps": len(tickets) / args.duration, "achieved_solves_per_s": len(ok) / span,
+            "offered_rps": len(tickets) / duration, "achieved_solves_per_s": len(ok) / span,
             "mean_queue_s": float(np.mean([r[1]["queue_s"] for r in ok])) if ok else None,
             "mean_run_s": float(np.mean([r[1]["run_s"] for r in ok])) if ok else None,
             "iterations_of_completed": [int(r[2]["iters"]) for r in ok][:50],
             "requests": [[specs[r[3]].n, specs[r[3]].k, round(r[1]["queue_s"], 4), round(r[1]["run_s"], 4),
                           round(r[1]["total_s"], 4)] for r in ok][:200],
             "queue_depth": depth[::max(1, len(depth) // 40)], "server_stats": st, "clocks": cs.summary()}
+
+
+def run_serve(args, ws, rank, local):
+    """Serving workload: Poisson arrivals (rate --rate) of solves, see
+    serve_measure.  value = p99 latency (arrival -> U on host) of the requests
+    that finished."""
+    import torch
+
+    import paper_2506_04045_b300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    m = serve_measure(args, rank, args.rate, args.duration, args.drain)
+    line = {"metric": "serving p99 latency (continuous batching)", "value": m["p99_s"],
+            "unit": "s", "n_gpus": ws, "steps": m["requests_submitted"], "warmup": 0, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", **m}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -268,10 +268,13 @@ static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, bo
 
 // ---- streaming update (tc_stream.cuh) ----
 static cudaError_t stream_setup_attr() {
-  cudaError_t e = cudaFuncSetAttribute(update_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)ts::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(update_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts::SMEM);
+  const void* fns[4] = {(const void*)update_stream_kernel<false, false>, (const void*)update_stream_kernel<false, true>,
+                        (const void*)update_stream_kernel<true, false>, (const void*)update_stream_kernel<true, true>};
+  for (const void* fn : fns) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Tensor maps of the iterate and product buffers (n x 32 float32): boxes of
@@ -316,8 +319,14 @@ static cluster_status make_stream_maps(cluster_ctx* c) {
 // the row-local update of a split pass with the context's engine
 static void launch_update_ctx(const cluster_ctx* c, const PassArgs& a, cudaStream_t s) {
   if (c->stream_update) {
-    if (c->mixed) update_stream_kernel<true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
-    else update_stream_kernel<false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+    const bool full = c->k == 32;
+    if (c->mixed) {
+      if (full) update_stream_kernel<true, true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+      else update_stream_kernel<true, false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+    } else {
+      if (full) update_stream_kernel<false, true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+      else update_stream_kernel<false, false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
+    }
   } else {
     kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
   }
