@@ -143,27 +143,35 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
 // arithmetic: add half of the 13 dropped bits' weight, then drop them.  The
 // rounding cvt.rna.tf32.f32 performs, without the conversion pipe.
 __device__ __forceinline__ uint32_t round11(uint32_t b) { return (b + 0x1000u) & 0xFFFFE000u; }
-// 3xTF32 split of four values: hi = round11(x), lo = round11(x - hi)
+// 3xTF32 split of four values: hi = round11(x), lo = x - hi, exact and at most
+// 2^-11 |x|; lo is not rounded: the tensor core reads its leading 11 bits, so
+// it drops at most 2^-21 |x| (2^-22 with a rounded lo)
 __device__ __forceinline__ void split11_store4(float* hi, float* lo, const float* v) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     h[q] = round11(__float_as_uint(v[q]));
-    l[q] = round11(__float_as_uint(v[q] - __uint_as_float(h[q])));
+    l[q] = __float_as_uint(v[q] - __uint_as_float(h[q]));
   }
   *reinterpret_cast<uint4*>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // float pairs g[8 CG + j] (high) / g[16 + 8 CG + j] (low), kept as bits, += v[j]
+// by Fast2Sum (Dekker): s = h + x, the add's rounding error x - (s - h) into
+// the low part.  Exact when |h| >= |x|, which holds for these running sums:
+// the entries of Xbar^T Xbar are sums of products of non-negative values, so
+// the running sum of the tile partials only grows (and Y^{n+1} differs from
+// Xbar^n by the small momentum term); the first tile adds to zero exactly.
 template <int CG>
 __device__ __forceinline__ void pair_acc8(uint32_t (&g)[32], const uint32_t (&v)[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    float h = __uint_as_float(g[8 * CG + j]), l = __uint_as_float(g[16 + 8 * CG + j]);
-    two_sum_acc(h, l, __uint_as_float(v[j]));
-    g[8 * CG + j] = __float_as_uint(h);
-    g[16 + 8 * CG + j] = __float_as_uint(l);
+    const float h = __uint_as_float(g[8 * CG + j]), x = __uint_as_float(v[j]);
+    const float sum = h + x;
+    const float err = x - (sum - h);
+    g[8 * CG + j] = __float_as_uint(sum);
+    g[16 + 8 * CG + j] = __float_as_uint(__uint_as_float(g[16 + 8 * CG + j]) + err);
   }
 }
 
@@ -564,6 +572,9 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
     pin32(pvu);
 #pragma unroll
     for (int f = 0; f < 32; ++f) pv[f] = __uint_as_float(pvu[f]);
+    // the scale 2^13, or 0 for a row past n (its operand row must be zero);
+    // s y^{n+1} = s xbar^n + (s beta_{n+1}) (xbar^n - xbar^{n-1})
+    const float rs = active ? kScale : 0.f, bs = beta_next * rs;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
       uint32_t hu[4], lu[4];
@@ -575,9 +586,8 @@ __device__ __forceinline__ void stream_compute(const PassArgs& a, const StreamCt
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int f = 8 * (ch & 3) + 2 * e + h;
-          const float xv = v[f];
-          const float g = ch < 4 ? xv : fmaf(beta_next, xv - pv[f], xv);
-          const float val = active ? g * kScale : 0.f;
+          const float xs = v[f] * rs;
+          const float val = ch < 4 ? xs : fmaf(bs, v[f] - pv[f], xs);
           hv[h] = __uint_as_float(round11(__float_as_uint(val)));
           lv[h] = val - hv[h];
         }
