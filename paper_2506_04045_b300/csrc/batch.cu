@@ -60,7 +60,7 @@ struct BOps {
     }
     return mixed ? batch_update_kernel<KP, true, false> : batch_update_kernel<KP, false, false>;
   }
-  static size_t upd_smem(bool tc) { return use_tc(tc) ? TcUpd<KP>::smem() : pass_smem_bytes<KP>(false); }
+  static size_t upd_smem(bool tc) { return use_tc(tc) ? TcUpd<KP>::smem() : update_smem_bytes<KP>(); }
   static cudaError_t setup() {
     for (int v = 0; v < (TcUpd<KP>::ON ? 4 : 2); ++v) {
       const bool mixed = v & 1, tc = v >> 1;

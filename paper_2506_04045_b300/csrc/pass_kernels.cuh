@@ -203,6 +203,30 @@ __host__ __device__ constexpr size_t pass_smem_bytes(bool eval) {
   return sizeof(float) * ((eval ? 0 : (size_t)L::E2) + (tiles > red ? tiles : red)) + 64;
 }
 
+// Split update (update_kernel, batch_update_kernel) for KP >= 64: the next
+// tile's four input rows (z, xbar^{n}, xbar^{n-1}, z^{prev}; 16 bytes per
+// lane) are staged in shared memory by cp.async while the current tile is
+// computed, behind the pass's own shared memory (the k = 64 class of the
+// batched workload: update 2.91 -> 2.78 ms; for KP = 16 and 32 the extra 16
+// KB cost a resident block per SM and time)
+template <int KP>
+__host__ __device__ constexpr bool update_prefetch() { return Lay<KP>::VEC == 4 && KP >= 64; }
+template <int KP>
+__host__ __device__ constexpr size_t update_stage_offset() { return (pass_smem_bytes<KP>(false) + 15) / 16 * 16; }
+template <int KP>
+__host__ __device__ constexpr size_t update_smem_bytes() {
+  return update_prefetch<KP>() ? update_stage_offset<KP>() + 4 * sizeof(float) * (size_t)Lay<KP>::R * KP
+                               : pass_smem_bytes<KP>(false);
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // One block's share of a pass: positions [p0, p1) of the row order, partial
 // results into slot `slot` of gram_part / sc_part.  `pass` is the index of the
 // newest iterate (the buffer parity), or the evaluated buffer when EVAL.
@@ -306,6 +330,20 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
 
   const int32_t* order = SPLIT ? nullptr : a.order;
   int64_t next_row = (p0 + team < p1) ? (order ? (int64_t)order[p0 + team] : p0 + team) : 0;
+  // split update: this lane's 16 bytes of the four input rows of the next tile
+  constexpr bool PF = SPLIT && update_prefetch<KP>();
+  float* stg = smem + update_stage_offset<KP>() / sizeof(float) + team * KP + f0;
+  constexpr int SSTR = L::R * KP;  // floats between the four staged arrays
+  auto stage = [&](int64_t r) {
+    cp_async16(stg, Zcur + r * KP + f0);
+    cp_async16(stg + SSTR, P + r * KP + f0);
+    cp_async16(stg + 2 * SSTR, Q + r * KP + f0);
+    cp_async16(stg + 3 * SSTR, Zprv + r * KP + f0);
+    cp_async_commit();
+  };
+  if constexpr (PF) {
+    if (p0 < p1) stage(next_row);
+  }
   for (int64_t base = p0; base < p1; base += L::R) {
     const int64_t pos = base + team;
     const bool active = pos < p1;
@@ -319,7 +357,19 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
     for (int q = 0; q < L::VEC; ++q) acc[q] = 0.f;
 
     int64_t lo = 0, hi = 0;
-    if constexpr (SPLIT) {
+    // own-row loads are independent of the gather: issue them first
+    float pv[L::VEC];
+    float qv[L::VEC], zp[L::VEC];
+    if constexpr (PF) {
+      // this tile's rows, staged during the previous tile (each lane reads back
+      // only the bytes its own copies wrote); then the next tile's copies
+      cp_async_wait_all();
+      load_row<L::VEC>(stg, acc);
+      load_row<L::VEC>(stg + SSTR, pv);
+      load_row<L::VEC>(stg + 2 * SSTR, qv);
+      load_row<L::VEC>(stg + 3 * SSTR, zp);
+      if (base + L::R < p1) stage(next_row);
+    } else if constexpr (SPLIT) {
       load_row<L::VEC>(Zcur + row * KP + f0, acc);
     } else if (active && pos < a.n_heavy) {
       // chunked row: sum the partial products in chunk order
@@ -334,13 +384,12 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
       lo = a.row_ptr[row];
       hi = a.row_ptr[row + 1];
     }
-    // own-row loads are independent of the gather: issue them first
-    float pv[L::VEC];
-    load_row<L::VEC>(P + row * KP + f0, pv);
-    float qv[L::VEC], zp[L::VEC];
-    if constexpr (!EVAL) {
-      load_row<L::VEC>(Q + row * KP + f0, qv);
-      load_row<L::VEC>((SPLIT ? Zprv : a.Zp) + row * KP + f0, zp);
+    if constexpr (!PF) {
+      load_row<L::VEC>(P + row * KP + f0, pv);
+      if constexpr (!EVAL) {
+        load_row<L::VEC>(Q + row * KP + f0, qv);
+        load_row<L::VEC>((SPLIT ? Zprv : a.Zp) + row * KP + f0, zp);
+      }
     }
     if constexpr (!SPLIT) {
       const int nb = (int)((hi - lo + L::NB - 1) / L::NB);

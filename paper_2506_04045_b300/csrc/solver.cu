@@ -122,7 +122,7 @@ struct KPOps {
         return tc_blocks_per_sm(fn, L::NT, TcUpd<KP>::smem(), TcUpd<KP>::TMEM_COLS);
       }
     }
-    const size_t smem = pass_smem_bytes<KP>(false);
+    const size_t smem = update_smem_bytes<KP>();
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, true>, L::NT, smem);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, update_kernel<KP, false>, L::NT, smem);
     return occ < 1 ? 1 : occ;
@@ -135,7 +135,7 @@ struct KPOps {
       e = cudaFuncSetAttribute(update_tc_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
     }
-    const int smem = (int)pass_smem_bytes<KP>(false);
+    const int smem = (int)update_smem_bytes<KP>();
     cudaError_t e = cudaFuncSetAttribute(update_kernel<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(update_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -177,7 +177,7 @@ struct KPOps {
         return;
       }
     }
-    const size_t smem = pass_smem_bytes<KP>(false);
+    const size_t smem = update_smem_bytes<KP>();
     if (mixed) update_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
     else update_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
   }
