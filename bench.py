@@ -699,26 +699,33 @@ def run_e2e(args, pkg, rp, col, val, U0, form, K, barrier, max_over_ranks):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e0.record(stream)
     for h, d in ((h_rp, d_rp), (h_col, d_col), (h_val, d_val), (h_U0, d_U0)):
         d.copy_(h, non_blocking=True)
+    ev[0].record(stream)
     s = pkg.Solver(d_rp, d_col, d_val, d_U0, stop_rule=pkg.STOP_NONE, max_iter=10 ** 9, borrow=1,
                    precision=pkg.MIXED_BF16 if mixed else pkg.FP32, fused_pass=1 if args.fused else 0,
                    relabel=args.relabel, update_engine=args.update_engine, overlap=args.overlap)
+    ev[1].record(stream)
     losses = []
     for _ in range(K):
         losses.append(s.step(1)["f"])
     U = s.get_U()
+    ev[2].record(stream)
     h_U.copy_(U, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    marks = [e0] + ev + [e1]
+    phases = {name: round(marks[i].elapsed_time(marks[i + 1]) / 1000.0, 4)
+              for i, name in enumerate(("h2d", "init", "iterations", "d2h"))}
     s.close()
     h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_col, h_val, h_U0))
     d2h = h_U.numel() * h_U.element_size() + K * 8
     return {"value": K / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d / K,
-            "d2h_bytes_per_step": d2h / K, "seconds": ms / 1000.0,
+            "d2h_bytes_per_step": d2h / K, "seconds": ms / 1000.0, "phases_s": phases,
             "note": "one solve: H2D of S and U0, cluster_init, K iterations each reading the loss, D2H of U"}
 
 

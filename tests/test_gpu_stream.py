@@ -81,6 +81,28 @@ def test_stream_update_k_and_precision(k, precision):
     assert maxabs(U.cpu().numpy(), Ub.cpu().numpy()) <= 1e-5
 
 
+# rows on faces of the simplex: most features of the start point are exactly
+# zero, and after 20 steps more than half of the rows still have a zero
+# feature, so the projection's active-set iteration runs for them (rows whose
+# features all exceed the first threshold skip it); k = 32 takes the
+# full-width kernel, k = 24 the padded one
+@pytest.mark.parametrize("k", [24, 32])
+def test_stream_update_projection_on_faces(k):
+    n = 3000
+    spec = synth.GraphSpec("dcsbm", n, k, 77 + k, mean_deg=20.0)
+    rp, c, v = synth.make_graph(spec, device="cuda")
+    U0 = synth.dirichlet_u0(n, k, 78 + k)
+    keep = (torch.arange(n * k).view(n, k) * 2654435761 % 97) < 12   # about 1 feature in 8
+    keep[:, 0] = True
+    U0 = U0 * keep
+    U0 = (U0 / U0.sum(dim=1, keepdim=True)).to(torch.float32).cuda()
+    U, _ = _run(rp, c, v, U0, 20, update_engine=STREAM)
+    _, o = _oracle(rp, c, v, U0, 20)
+    assert (o.U == 0.0).mean() > 0.02                      # the faces are reached
+    assert ((o.U > 0.0).sum(axis=1) < k).mean() > 0.4
+    assert maxabs(U.cpu().numpy(), o.U) <= 1e-5
+
+
 def test_stream_update_reruns_and_resume_are_bit_identical():
     spec = synth.GraphSpec("dcsbm", 40000, 32, 541, mean_deg=25.0)
     rp, c, v = synth.make_graph(spec, device="cuda")
