@@ -915,58 +915,85 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
 // Gram partials of one iterate buffer without any product with S (the solver's
 // start: G(Y^1) = Xbar^0^T Xbar^0 and ||Xbar^0^T Xbar^0||^2; the loss of Xbar^0
 // comes from the first pass, whose product with S forms its trace term).
-// Block b takes rows [b n / grid, (b+1) n / grid) in tiles of 32 staged in
-// shared memory, the next tile's loads in flight while a tile is summed;
-// thread t owns entries t, t + 256, ... of the KP x KP matrix, sums each tile
-// in float32 and the tiles in float64, and writes the block's partial into
-// gram_part[b][0] (sc_part[b] = 0: no trace term).
+// Block b takes rows [b n / grid, (b+1) n / grid) in tiles of TR rows staged in
+// shared memory, the next tile's loads in flight while a tile is summed.  The
+// KP x KP matrix is cut into B x B register blocks (B = 4; KP = 2: one 2 x 2
+// block); the 256 threads are NBLK blocks x GRP row groups, and thread (g, blk)
+// sums rows g, g + GRP, ... of each tile for its block: per row two short
+// shared-memory reads feed B^2 FMAs (one read per FMA was the shared-memory
+// bandwidth bound: 17 ms at n = 70M, k = 32).  Float32 sums over 32 rows of a
+// thread, float64 across them; the row groups are added in group order
+// (fixed: deterministic); the block's partial goes to gram_part[b][0]
+// (sc_part[b] = 0: no trace term).
 template <int KP>
 __global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X, int64_t n, float* gram_part,
                                                     double* sc_part) {
-  static_assert(KP <= 64, "per-thread entries");
-  constexpr int E2 = KP * KP, EPT = (E2 + 255) / 256, TR = 32, LPT = TR * KP / 256;
-  static_assert(LPT * 256 == TR * KP || KP < 8, "tile loads per thread");
-  constexpr int LP = LPT > 0 ? LPT : 1;
-  __shared__ float tile[TR * KP];
+  static_assert(KP <= 64, "register blocks");
+  constexpr int E2 = KP * KP;
+  constexpr int B = KP >= 4 ? 4 : KP;
+  constexpr int NBS = KP / B, NBLK = NBS * NBS, GRP = 256 / NBLK;
+  static_assert(NBLK * GRP == 256, "blocks x row groups = threads");
+  constexpr int TR = GRP > 32 ? GRP : 32;          // rows per tile
+  constexpr int RPT = TR / GRP;                     // rows of a tile per thread
+  constexpr int TPF = 32 / RPT > 0 ? 32 / RPT : 1;  // tiles summed in float32 between float64 adds
+  constexpr int LP = TR * KP / 256;                 // tile elements loaded per thread
+  static_assert(LP * 256 == TR * KP, "tile loads per thread");
+  __shared__ __align__(16) float tile[TR * KP];
+  __shared__ double red[256 * B * B];
   const int tid = threadIdx.x;
+  const int g = tid / NBLK, blk = tid % NBLK, bi = blk / NBS, bj = blk % NBS;
   const int64_t p0 = n * (int64_t)blockIdx.x / gridDim.x, p1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-  double acc[EPT];
+  double acc[B * B];
+  float t[B * B];
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) acc[q] = 0.0;
+  for (int q = 0; q < B * B; ++q) acc[q] = 0.0, t[q] = 0.0f;
   // element e of the tile at row base: X[base KP + e] for rows below p1, else 0
   auto fetch = [&](int64_t base, float* v) {
 #pragma unroll
     for (int l = 0; l < LP; ++l) {
       const int e = tid + l * 256;
-      v[l] = (e < TR * KP && base + e / KP < p1) ? __ldg(X + base * KP + e) : 0.0f;
+      v[l] = (base + e / KP < p1) ? __ldg(X + base * KP + e) : 0.0f;
     }
   };
   float nxt[LP];
   if (p0 < p1) fetch(p0, nxt);
+  int since = 0;
   for (int64_t base = p0; base < p1; base += TR) {
 #pragma unroll
-    for (int l = 0; l < LP; ++l)
-      if (tid + l * 256 < TR * KP) tile[tid + l * 256] = nxt[l];
+    for (int l = 0; l < LP; ++l) tile[tid + l * 256] = nxt[l];
     __syncthreads();
     if (base + TR < p1) fetch(base + TR, nxt);
+#pragma unroll 4
+    for (int rr = 0; rr < RPT; ++rr) {
+      const float* row = tile + (g + rr * GRP) * KP;
+      float a[B], b[B];
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * 256;
-      if (e < E2) {
-        const int i = e / KP, j = e % KP;
-        float t = 0.0f;
-#pragma unroll 8
-        for (int r = 0; r < TR; ++r) t = fmaf(tile[r * KP + i], tile[r * KP + j], t);
-        acc[q] += (double)t;
+      for (int p = 0; p < B; ++p) {
+        a[p] = row[bi * B + p];
+        b[p] = row[bj * B + p];
       }
+#pragma unroll
+      for (int p = 0; p < B; ++p)
+#pragma unroll
+        for (int q = 0; q < B; ++q) t[p * B + q] = fmaf(a[p], b[q], t[p * B + q]);
+    }
+    if (++since == TPF) {
+#pragma unroll
+      for (int q = 0; q < B * B; ++q) acc[q] += (double)t[q], t[q] = 0.0f;
+      since = 0;
     }
     __syncthreads();
   }
-  float* go = gram_part + (size_t)blockIdx.x * 2 * E2;
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * 256;
-    if (e < E2) go[e] = (float)acc[q];
+  for (int q = 0; q < B * B; ++q) red[tid * B * B + q] = acc[q] + (double)t[q];
+  __syncthreads();
+  float* go = gram_part + (size_t)blockIdx.x * 2 * E2;
+  for (int e = tid; e < E2; e += 256) {
+    const int i = e / KP, j = e % KP;
+    const int eb = (i / B) * NBS + j / B, ep = (i % B) * B + j % B;
+    double sum = 0.0;
+    for (int gg = 0; gg < GRP; ++gg) sum += red[(gg * NBLK + eb) * B * B + ep];
+    go[e] = (float)sum;
   }
   if (tid < 4) sc_part[blockIdx.x * 4 + tid] = 0.0;
 }

@@ -142,9 +142,17 @@ def test_loss_stop_rule_matches_oracle():
     S = to_scipy(rp, c, v, spec.n)
     U0 = synth.dirichlet_u0(spec.n, 8, 21)
     tau = 30.0 / oracle.lipschitz(S)          # large step: the loss test fires after a few dozen iterations
-    o = oracle.fista(S, U0.numpy().astype(np.float64), tau, tol=1e-3 * spec.n, max_iter=400)
-    assert o.stopped and o.iters < 400
-    s, _ = _solver(rp, c, v, U0, step_rule=pkg.STEP_CONST, tau=tau, tol=1e-3 * spec.n, max_iter=400)
+    # the tolerance sits midway between two consecutive decrements of the
+    # oracle's loss (about 0.2 from each, 7e-7 of f), so that the decision is
+    # far outside the float32 accuracy of the loss difference
+    free = oracle.fista(S, U0.numpy().astype(np.float64), tau, max_iter=120, stop="none")
+    dec = -np.diff(np.asarray(free.losses))
+    m = int(np.nonzero(dec <= 5.0)[0][0])
+    tol = 0.5 * (dec[m - 1] + dec[m])
+    assert np.min(np.abs(dec[: m + 1] - tol)) > 0.15   # no decrement up to there is near tol
+    o = oracle.fista(S, U0.numpy().astype(np.float64), tau, tol=tol, max_iter=400)
+    assert o.stopped and o.iters == m + 1
+    s, _ = _solver(rp, c, v, U0, step_rule=pkg.STEP_CONST, tau=tau, tol=tol, max_iter=400)
     rep = s.solve()
     assert rep["done"] == 1 and rep["status"] == pkg.OK
     assert rep["out_iter"] == o.iters
