@@ -915,16 +915,25 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
 // Gram partials of one iterate buffer without any product with S (the solver's
 // start: G(Y^1) = Xbar^0^T Xbar^0 and ||Xbar^0^T Xbar^0||^2; the loss of Xbar^0
 // comes from the first pass, whose product with S forms its trace term).
-// Block b takes rows [b n / grid, (b+1) n / grid) in tiles of TR rows staged in
-// shared memory, the next tile's loads in flight while a tile is summed.  The
+// Block b takes rows [b n / grid, (b+1) n / grid) in tiles of TR rows, staged in
+// shared memory by cp.async two tiles deep (16 KB per tile at k = 32, so that
+// enough bytes are in flight), rows past the block's range read as zero.  The
 // KP x KP matrix is cut into B x B register blocks (B = 4; KP = 2: one 2 x 2
 // block); the 256 threads are NBLK blocks x GRP row groups, and thread (g, blk)
 // sums rows g, g + GRP, ... of each tile for its block: per row two short
 // shared-memory reads feed B^2 FMAs (one read per FMA was the shared-memory
 // bandwidth bound: 17 ms at n = 70M, k = 32).  Float32 sums over 32 rows of a
-// thread, float64 across them; the row groups are added in group order
-// (fixed: deterministic); the block's partial goes to gram_part[b][0]
-// (sc_part[b] = 0: no trace term).
+// thread, added into float pairs by Fast2Sum (exact here: the entries are sums
+// of products of non-negative values, so the running sums only grow; float64
+// adds, on B300's narrow float64 pipe, were the next bound); the row groups
+// are added in float64 in group order (fixed: deterministic); the block's
+// partial goes to gram_part[b][0] (sc_part[b] = 0: no trace term).
+template <int KP>
+__host__ __device__ constexpr int gram0_rows_per_tile() {
+  return (256 / ((KP / (KP >= 4 ? 4 : KP)) * (KP / (KP >= 4 ? 4 : KP)))) > 128
+             ? 256 / ((KP / (KP >= 4 ? 4 : KP)) * (KP / (KP >= 4 ? 4 : KP)))
+             : (KP == 64 ? 64 : 128);
+}
 template <int KP>
 __global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X, int64_t n, float* gram_part,
                                                     double* sc_part) {
@@ -933,44 +942,66 @@ __global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X,
   constexpr int B = KP >= 4 ? 4 : KP;
   constexpr int NBS = KP / B, NBLK = NBS * NBS, GRP = 256 / NBLK;
   static_assert(NBLK * GRP == 256, "blocks x row groups = threads");
-  constexpr int TR = GRP > 32 ? GRP : 32;          // rows per tile
+  constexpr int TR = gram0_rows_per_tile<KP>();     // rows per tile
+  static_assert(TR % GRP == 0, "row groups tile the rows");
   constexpr int RPT = TR / GRP;                     // rows of a tile per thread
   constexpr int TPF = 32 / RPT > 0 ? 32 / RPT : 1;  // tiles summed in float32 between float64 adds
-  constexpr int LP = TR * KP / 256;                 // tile elements loaded per thread
-  static_assert(LP * 256 == TR * KP, "tile loads per thread");
-  __shared__ __align__(16) float tile[TR * KP];
-  __shared__ double red[256 * B * B];
+  constexpr int CB = KP * 4 >= 16 ? 16 : KP * 4;    // bytes per cp.async (whole rows' pieces)
+  constexpr int CF = CB / 4;                        // floats per cp.async
+  constexpr int NCH = TR * KP / CF;                 // cp.async per tile
+  constexpr int TILE_F = TR * KP;
+  constexpr int BUF_B = 2 * TILE_F * 4 > 256 * B * B * 8 ? 2 * TILE_F * 4 : 256 * B * B * 8;
+  __shared__ __align__(16) unsigned char smem_raw[BUF_B];
+  float* tiles = reinterpret_cast<float*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw);   // after the last tile
   const int tid = threadIdx.x;
   const int g = tid / NBLK, blk = tid % NBLK, bi = blk / NBS, bj = blk % NBS;
   const int64_t p0 = n * (int64_t)blockIdx.x / gridDim.x, p1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-  double acc[B * B];
-  float t[B * B];
+  float ah[B * B], al[B * B], t[B * B];
 #pragma unroll
-  for (int q = 0; q < B * B; ++q) acc[q] = 0.0, t[q] = 0.0f;
-  // element e of the tile at row base: X[base KP + e] for rows below p1, else 0
-  auto fetch = [&](int64_t base, float* v) {
-#pragma unroll
-    for (int l = 0; l < LP; ++l) {
-      const int e = tid + l * 256;
-      v[l] = (base + e / KP < p1) ? __ldg(X + base * KP + e) : 0.0f;
+  for (int q = 0; q < B * B; ++q) ah[q] = 0.0f, al[q] = 0.0f, t[q] = 0.0f;
+  // tile at row base into buffer b: rows below p1 copied, the rest zero-filled
+  auto stage = [&](int64_t base, int b) {
+    float* dst = tiles + b * TILE_F;
+    for (int c = tid; c < NCH; c += 256) {
+      const int64_t row = base + (c * CF) / KP;
+      const bool in = row < p1;
+      const float* src = in ? X + base * KP + (int64_t)c * CF : X;
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + c * CF);
+      if constexpr (CB == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(CB), "r"(in ? CB : 0)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  float nxt[LP];
-  if (p0 < p1) fetch(p0, nxt);
-  int since = 0;
+  int since = 0, cur = 0;
+  if (p0 < p1) stage(p0, 0);
   for (int64_t base = p0; base < p1; base += TR) {
-#pragma unroll
-    for (int l = 0; l < LP; ++l) tile[tid + l * 256] = nxt[l];
+    if (base + TR < p1) {
+      stage(base + TR, cur ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     __syncthreads();
-    if (base + TR < p1) fetch(base + TR, nxt);
+    const float* tile = tiles + cur * TILE_F;
 #pragma unroll 4
     for (int rr = 0; rr < RPT; ++rr) {
       const float* row = tile + (g + rr * GRP) * KP;
       float a[B], b[B];
+      if constexpr (B == 4) {  // 16-byte reads (rows and blocks are 16-byte aligned)
+        const float4 va = *reinterpret_cast<const float4*>(row + bi * B);
+        const float4 vb = *reinterpret_cast<const float4*>(row + bj * B);
+        a[0] = va.x, a[1] = va.y, a[2] = va.z, a[3] = va.w;
+        b[0] = vb.x, b[1] = vb.y, b[2] = vb.z, b[3] = vb.w;
+      } else {
 #pragma unroll
-      for (int p = 0; p < B; ++p) {
-        a[p] = row[bi * B + p];
-        b[p] = row[bj * B + p];
+        for (int p = 0; p < B; ++p) {
+          a[p] = row[bi * B + p];
+          b[p] = row[bj * B + p];
+        }
       }
 #pragma unroll
       for (int p = 0; p < B; ++p)
@@ -979,13 +1010,19 @@ __global__ void __launch_bounds__(256) gram0_kernel(const float* __restrict__ X,
     }
     if (++since == TPF) {
 #pragma unroll
-      for (int q = 0; q < B * B; ++q) acc[q] += (double)t[q], t[q] = 0.0f;
+      for (int q = 0; q < B * B; ++q) {
+        const float sum = ah[q] + t[q];
+        al[q] += t[q] - (sum - ah[q]);
+        ah[q] = sum;
+        t[q] = 0.0f;
+      }
       since = 0;
     }
-    __syncthreads();
+    __syncthreads();   // the buffer just read is staged into two tiles from now
+    cur ^= 1;
   }
 #pragma unroll
-  for (int q = 0; q < B * B; ++q) red[tid * B * B + q] = acc[q] + (double)t[q];
+  for (int q = 0; q < B * B; ++q) red[tid * B * B + q] = ((double)ah[q] + (double)al[q]) + (double)t[q];
   __syncthreads();
   float* go = gram_part + (size_t)blockIdx.x * 2 * E2;
   for (int e = tid; e < E2; e += 256) {

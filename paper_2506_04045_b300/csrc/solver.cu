@@ -184,6 +184,11 @@ struct KPOps {
   static void launch_gram0(const float* X, int64_t n, float* gp, double* sp, int grid, cudaStream_t s) {
     if constexpr (KP <= 64) gram0_kernel<KP><<<grid, 256, 0, s>>>(X, n, gp, sp);
   }
+  static int occ_gram0() {
+    int occ = 1;
+    if constexpr (KP <= 64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram0_kernel<KP>, 256, 0);
+    return occ < 1 ? 1 : occ;
+  }
   static void launch_fold(const FoldArgs& f, cudaStream_t s) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
     fold_kernel<KP><<<(nent + fold_epb<KP>() - 1) / fold_epb<KP>(), 256, 0, s>>>(f);
@@ -226,6 +231,11 @@ static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, boo
   FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static int kp_occ_gram0(int KP) {
+  int o = 1;
+  FC_DISPATCH(KP, o = Ops::occ_gram0());
+  return o;
+}
 static void kp_launch_gram0(int KP, const float* X, int64_t n, float* gp, double* sp, int grid, cudaStream_t s) {
   FC_DISPATCH(KP, Ops::launch_gram0(X, n, gp, sp, grid, s));
 }
@@ -908,9 +918,10 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   // term of f(Xbar^0), and its fold the loss (f_iter stays -1 until then).
   // k = 128: one objective-only pass (also f(Xbar^0) at once).
   if (c->KP <= 64) {
-    // as many blocks as partial slots, up to 8 resident per SM, at least a tile each
+    // one wave of resident blocks (at most one per partial slot, at least 32 rows each)
     const int slots = std::max(c->parts, c->parts_upd);
-    const int g0 = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)slots, (int64_t)sms * 8, (n + 31) / 32}));
+    const int g0 = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)slots, (int64_t)sms * kp_occ_gram0(c->KP), (n + 31) / 32}));
     kp_launch_gram0(c->KP, c->X[0], n, c->gram_part, c->sc_part, g0, s);
     FoldArgs f0 = make_fold_args(c, 1, 1);
     f0.parts = g0;
