@@ -70,6 +70,8 @@ def parse():
                         "(the 512-instance batch, --extra-steps timed iterations), serve (a Poisson stream at "
                         "--extra-serve-rate); empty to skip")
     p.add_argument("--extra-steps", type=int, default=10)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="batch: keep the default launch shapes (no autotuner trials, e.g. for a clean ncu launch list)")
     p.add_argument("--extra-serve-rate", type=float, default=0.5)
     p.add_argument("--extra-serve-duration", type=float, default=20.0)
     p.add_argument("--extra-serve-drain", type=float, default=25.0)
@@ -757,7 +759,7 @@ def batch_measure(args, ranks, rank, K, W, forms):
                       precision=pkg.MIXED_BF16 if mixed else pkg.FP32, relabel=args.relabel,
                       update_engine=args.update_engine, overlap=args.overlap)
         init_s = time.perf_counter() - t1
-        desc = b.autotune(trials=1)
+        desc = b.describe() if args.no_autotune else b.autotune(trials=1)
         b.step(W)
         torch.cuda.synchronize()
         ranks.barrier()
