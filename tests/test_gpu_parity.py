@@ -195,6 +195,28 @@ def test_planted_factor_fixed_point_bit_exact():
     assert rep["f"] <= 1e-6 * n
 
 
+# the start: after one pass the solver reports f(Xbar^0), whose Gram term comes
+# from the start Gram (gram0_kernel: k <= 64, register blocks of 4 x 4 or 2 x 2,
+# tiles of 64 to 256 rows, rows past a block's range zero-filled) and whose trace
+# term from the first product with S; sizes below one tile, a ragged last tile,
+# and many blocks
+@pytest.mark.parametrize("k", [2, 3, 5, 8, 13, 16, 27, 32, 48, 64])
+@pytest.mark.parametrize("n", [37, 1000, 20011])
+def test_start_gram_and_loss_of_the_start_point(k, n):
+    spec = synth.GraphSpec("dcsbm", n, k, 900 + k + n, mean_deg=min(20.0, n / 4.0))
+    rp, c, v = synth.make_graph(spec)
+    U0 = synth.dirichlet_u0(n, k, 901 + k)
+    s, _ = _solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=1)
+    rep = s.step(1)
+    s.close()
+    assert rep["f_iter"] == 0
+    S = to_scipy(rp, c, v, n)
+    terms = oracle.loss_terms(S, U0.numpy().astype(np.float64))
+    assert abs(rep["gram_fro2"] - terms["gram_fro2"]) <= 1e-6 * terms["gram_fro2"]
+    f0 = oracle.objective_trace(S, U0.numpy().astype(np.float64))
+    assert abs(rep["f"] - f0) <= TOL_F * f0
+
+
 def test_objective_entry_point():
     for spec, k in [(synth.GraphSpec("dcsbm", 5000, 32, 31, mean_deg=30.0), 32),
                     (synth.GraphSpec("sbm", 2000, 8, 0), 7)]:
