@@ -66,6 +66,18 @@ __device__ __forceinline__ void gram_task(int t, int nblk, int nb1, int& m, int&
   J = I + bi;
 }
 
+// Block b (row order) of the 16 x 8 blocks (mi, nj) with nj >= 2 mi of a
+// matrix with nbj block columns: the blocks holding entries on or above the
+// diagonal.
+__device__ __forceinline__ void tri_block(int b, int nbj, int& mi, int& nj) {
+  mi = 0;
+  while (b >= nbj - 2 * mi) {
+    b -= nbj - 2 * mi;
+    ++mi;
+  }
+  nj = 2 * mi + b;
+}
+
 // ---- warp-level tensor-core helpers (mma.sync m16n8k8, TF32 inputs, FP32 accumulate) ----
 // Fragment layout (lane = 4 g + t): A 16x8 row-major a0 = A[g][t], a1 = A[g+8][t],
 // a2 = A[g][t+4], a3 = A[g+8][t+4]; B 8x8 b0 = B[t][g], b1 = B[t+4][g];
@@ -99,15 +111,27 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint
 // is written to shared memory.  Strides: TSA (= 4 mod 32 in words) makes the
 // row-major fragment reads conflict-free, TSB (= 8 mod 16) the transposed
 // Gram reads and the float2 stores of Y G.
+//
+// KP = 128 (the update only, not the objective-only pass): the same Y G; the
+// Gram blocks are only those on or above the diagonal (16 x 8 blocks
+// (mi, nj) with nj >= 2 mi: the fold reads the upper triangle), TRIB per
+// matrix, spread evenly over the warps (TPW_B per warp, in (matrix, mi, nj)
+// order, so a warp's A fragment changes at most once or twice): the full
+// square would need 16 blocks of accumulators per warp, beyond the register
+// budget of a 512-thread block.
 template <int KP, bool EVAL>
 struct MmaLay {
-  static constexpr bool ON = KP >= 16 && KP <= 64;
+  static constexpr bool TRI = KP == 128 && !EVAL;
+  static constexpr bool ON = (KP >= 16 && KP <= 64) || TRI;
   static constexpr int TSA = KP + 4;
   static constexpr int TSB = KP + 8;
   static constexpr int KS = KP / 8;                     // K steps of Y G
   static constexpr int MATS = EVAL ? 1 : 2;
   static constexpr int GBLK = ON ? (KP / 16) * (KP / 8) : 1;  // 16x8 blocks per matrix
-  static constexpr int TB = MATS * GBLK;
+  static constexpr int TRIB = (KP / 16) * (KP / 16 + 1);        // blocks with nj >= 2 mi per matrix
+  static constexpr int TPW_B = TRI ? MATS * TRIB / Lay<KP>::WARPS : 1;
+  static_assert(!TRI || TPW_B * Lay<KP>::WARPS == MATS * TRIB, "triangle blocks per warp");
+  static constexpr int TB = TRI ? Lay<KP>::WARPS : MATS * GBLK;
   static constexpr int WARPS = Lay<KP>::WARPS;
   static constexpr int KSPLIT = TB >= WARPS ? 1 : WARPS / TB;
   static constexpr int BPW = TB >= WARPS ? TB / WARPS : 1;
@@ -291,6 +315,17 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   }
   __syncthreads();
 
+  // KP = 128: this warp's triangle blocks, decoded once: mat << 16 | mi << 8 | nj
+  __shared__ int tri_tab[M::TRI ? L::WARPS * M::TPW_B : 1];
+  if constexpr (M::TRI) {
+    if (lane < M::TPW_B) {
+      const int bb = warp * M::TPW_B + lane;
+      int mi, nj;
+      tri_block(bb % M::TRIB, KP / 8, mi, nj);
+      tri_tab[warp * M::TPW_B + lane] = ((bb / M::TRIB) << 16) | (mi << 8) | nj;
+    }
+    __syncwarp();
+  }
   // Gram blocks of this warp (MMA path)
   const int mb0 = M::ON ? (warp % (M::TB / M::BPW)) * M::BPW : 0;   // first block
   const int mks = M::ON ? warp / (M::TB / M::BPW) : 0;                // row-split part
@@ -298,9 +333,10 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   const int mmat = mb0 / (M::GBLK > 0 ? M::GBLK : 1);
   const int mrem = mb0 % (M::GBLK > 0 ? M::GBLK : 1);
   const int mmi = mrem / (KP / 8 > 0 ? KP / 8 : 1), mnj0 = mrem % (KP / 8 > 0 ? KP / 8 : 1);
-  float macc[M::ON ? M::BPW : 1][4];
+  constexpr int MACC = M::ON ? (M::TRI ? M::TPW_B : M::BPW) : 1;
+  float macc[MACC][4];
 #pragma unroll
-  for (int j = 0; j < (M::ON ? M::BPW : 1); ++j) macc[j][0] = macc[j][1] = macc[j][2] = macc[j][3] = 0.f;
+  for (int j = 0; j < MACC; ++j) macc[j][0] = macc[j][1] = macc[j][2] = macc[j][3] = 0.f;
 
   // Gram tasks of this thread (see GramLay)
   using G = GramLay<KP, EVAL>;
@@ -419,13 +455,20 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
         float dq[4] = {0.f, 0.f, 0.f, 0.f};
         const uint32_t* yh = reinterpret_cast<const uint32_t*>(ys) + (16 * ym + mg) * M::TSA + mt;
         const uint32_t* yl = reinterpret_cast<const uint32_t*>(ysl) + (16 * ym + mg) * M::TSA + mt;
+        // KP = 128: the K steps alternate between two accumulators (two
+        // dependency chains of 24 MMAs instead of one of 48), added at the end
+        float dq2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int ks = 0; ks < M::KS; ++ks) {
           const uint32_t ah[4] = {yh[8 * ks], yh[8 * M::TSA + 8 * ks], yh[8 * ks + 4], yh[8 * M::TSA + 8 * ks + 4]};
           const uint32_t al[4] = {yl[8 * ks], yl[8 * M::TSA + 8 * ks], yl[8 * ks + 4], yl[8 * M::TSA + 8 * ks + 4]};
           const uint4 g = Gf[(yn * M::KS + ks) * 32 + lane];
           const uint32_t bh[2] = {g.x, g.y}, bl[2] = {g.z, g.w};
-          mma3_tf32(dq, ah, al, bh, bl);
+          mma3_tf32((M::TRI && (ks & 1)) ? dq2 : dq, ah, al, bh, bl);
+        }
+        if constexpr (M::TRI) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dq[q] += dq2[q];
         }
         float* qo = qs + (16 * ym + mg) * TS + 8 * yn + 2 * mt;
         *reinterpret_cast<float2*>(qo) = make_float2(dq[0], dq[1]);
@@ -502,7 +545,47 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
       // The tensor core's accumulator addition does not round to nearest, so a
       // long running sum in it drifts; each tile's blocks start from zero and
       // are added to the running sums with ordinary float adds.
-      if (mon) {
+      if constexpr (M::TRI) {
+        // this warp's TPW_B blocks of the upper triangles, the A fragment
+        // reloaded only when the block row changes
+        float dt[M::TPW_B][4];
+#pragma unroll
+        for (int j = 0; j < M::TPW_B; ++j) dt[j][0] = dt[j][1] = dt[j][2] = dt[j][3] = 0.f;
+        uint32_t ah[M::RS][4], al[M::RS][4];
+        int cur = -1;
+#pragma unroll
+        for (int j = 0; j < M::TPW_B; ++j) {
+          const int info = tri_tab[warp * M::TPW_B + j];
+          const int mat = info >> 16, mi = (info >> 8) & 0xff, nj = info & 0xff;
+          const uint32_t* th = reinterpret_cast<const uint32_t*>(mat ? yn_t : xn_t);
+          const uint32_t* tl = reinterpret_cast<const uint32_t*>(mat ? yn_l : xn_l);
+          if ((info >> 8) != cur) {  // warp-uniform: (mat, mi) changed
+            cur = info >> 8;
+#pragma unroll
+            for (int rs = 0; rs < M::RS; ++rs) {
+              const int o0 = (8 * rs + mt) * TS, o4 = o0 + 4 * TS, ca = 16 * mi + mg;
+              ah[rs][0] = th[o0 + ca];
+              ah[rs][1] = th[o0 + ca + 8];
+              ah[rs][2] = th[o4 + ca];
+              ah[rs][3] = th[o4 + ca + 8];
+              al[rs][0] = tl[o0 + ca];
+              al[rs][1] = tl[o0 + ca + 8];
+              al[rs][2] = tl[o4 + ca];
+              al[rs][3] = tl[o4 + ca + 8];
+            }
+          }
+#pragma unroll
+          for (int rs = 0; rs < M::RS; ++rs) {
+            const int o0 = (8 * rs + mt) * TS, o4 = o0 + 4 * TS, cb = 8 * nj + mg;
+            const uint32_t bh[2] = {th[o0 + cb], th[o4 + cb]}, bl[2] = {tl[o0 + cb], tl[o4 + cb]};
+            mma3_tf32(dt[j], ah[rs], al[rs], bh, bl);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < M::TPW_B; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) macc[j][q] += dt[j][q];
+      } else if (mon) {
         const uint32_t* th = reinterpret_cast<const uint32_t*>(mmat ? yn_t : xn_t);
         const uint32_t* tl = reinterpret_cast<const uint32_t*>(mmat ? yn_l : xn_l);
         float dt[M::BPW][4];
@@ -580,7 +663,18 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
   float* gout = a.gram_part + (size_t)slot * 2 * L::E2;
   if constexpr (M::ON) {
     // block (mat, 16 mi.., 8 nj..) of fragment lane (mg, mt): rows mg, mg + 8, columns 2 mt, 2 mt + 1
-    if constexpr (M::KSPLIT == 1) {
+    if constexpr (M::TRI) {
+#pragma unroll
+      for (int j = 0; j < M::TPW_B; ++j) {
+        const int bb = warp * M::TPW_B + j;
+        const int mat = bb / M::TRIB;
+        int mi, nj;
+        tri_block(bb % M::TRIB, KP / 8, mi, nj);
+        float* o = gout + mat * L::E2 + (16 * mi + mg) * KP + 8 * nj + 2 * mt;
+        *reinterpret_cast<float2*>(o) = make_float2(macc[j][0], macc[j][1]);
+        *reinterpret_cast<float2*>(o + 8 * KP) = make_float2(macc[j][2], macc[j][3]);
+      }
+    } else if constexpr (M::KSPLIT == 1) {
 #pragma unroll
       for (int j = 0; j < M::BPW; ++j) {
         float* o = gout + mmat * L::E2 + (16 * mmi + mg) * KP + 8 * (mnj0 + j) + 2 * mt;
@@ -735,8 +829,9 @@ struct FoldArgs {
 // stores G(Y^{n+1}) minus its mean entry in float32 (the mean shift leaves the
 // projection unchanged because rows of Y sum to one: P(v + c 1) = P(v)).
 // First stage: each block sums the partials of FOLD_EPB entries, its 256
-// threads split into 256 / FOLD_EPB groups that take every group-th partial;
-// the group sums are then added in group order (a fixed tree: deterministic).
+// threads split into 256 / FOLD_EPB groups that take every group-th partial
+// (in four interleaved float-pair chains); the group sums are then added in
+// float64 in group order (a fixed tree: deterministic).
 template <int KP>
 __host__ __device__ constexpr int fold_epb() {
   return KP <= 32 ? 32 : (KP == 64 ? 64 : 128);
@@ -767,7 +862,24 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
     if (e < nent) {
       const int m = e / E2, r = (e % E2) / KP, c = e % KP;
       src = m * E2 + ((r <= c) ? r * KP + c : c * KP + r);
-      for (int p = g; p < f.parts; p += GR) s += (double)f.gram_part[(size_t)p * 2 * E2 + src];
+      // four chains over this group's partials (p, p + GR, p + 2 GR, p + 3 GR),
+      // each a float pair (TwoSum: the rounding error of every add kept,
+      // about 48 significant bits), converted to float64 once: float64 adds
+      // and conversions per partial saturated B300's narrow float64 pipe
+      const float* gp = f.gram_part + src;
+      const size_t st = (size_t)2 * E2 * GR;
+      float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+      int p = g;
+      for (; p + 3 * GR < f.parts; p += 4 * GR) {
+        const float* q = gp + (size_t)p * 2 * E2;
+        two_sum_acc(h[0], l[0], q[0]);
+        two_sum_acc(h[1], l[1], q[st]);
+        two_sum_acc(h[2], l[2], q[2 * st]);
+        two_sum_acc(h[3], l[3], q[3 * st]);
+      }
+      for (; p < f.parts; p += GR) two_sum_acc(h[0], l[0], gp[(size_t)p * 2 * E2]);
+      s = (((double)h[0] + (double)l[0]) + ((double)h[1] + (double)l[1])) +
+          (((double)h[2] + (double)l[2]) + ((double)h[3] + (double)l[3]));
     }
     gsum[tid] = s;
     __syncthreads();
@@ -788,11 +900,19 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
 
   __shared__ double red[256];
   const int k = st->k;
-  // ||A||_F^2 (fixed-order tree)
+  // ||A||_F^2 (fixed-order tree; each thread's entries in four chains, all
+  // loads issued up front: E2 / 256 of them, 64 at k = 128)
   double part = 0.0;
-  for (int i = tid; i < E2; i += 256) {
-    const double v = __ldcg(f.A + i);
-    part += v * v;
+  {
+    constexpr int PT = (E2 + 255) / 256;
+    double p4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+      const int i = tid + j * 256;
+      const double v = i < E2 ? __ldcg(f.A + i) : 0.0;
+      p4[j & 3] = fma(v, v, p4[j & 3]);
+    }
+    part = (p4[0] + p4[1]) + (p4[2] + p4[3]);
   }
   red[tid] = part;
   __syncthreads();
@@ -888,9 +1008,16 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   if (!f.eval || f.eval_init) {
     const double* Gsrc = f.eval ? f.A : f.G;
     double msum = 0.0;
-    for (int i = tid; i < E2; i += 256) {
-      const int r = i / KP, c = i % KP;
-      if (r < k && c < k) msum += __ldcg(Gsrc + i);
+    {
+      constexpr int PT = (E2 + 255) / 256;
+      double m4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < PT; ++j) {
+        const int i = tid + j * 256;
+        const int r = i / KP, c = i % KP;
+        if (i < E2 && r < k && c < k) m4[j & 3] += __ldcg(Gsrc + i);
+      }
+      msum = (m4[0] + m4[1]) + (m4[2] + m4[3]);
     }
     red[tid] = msum;
     __syncthreads();
@@ -899,6 +1026,7 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
       __syncthreads();
     }
     const double mean = red[0] / ((double)k * (double)k);
+#pragma unroll 8
     for (int i = tid; i < E2; i += 256) {
       const int r = i / KP, c = i % KP;
       f.Gy[i] = (r < k && c < k) ? (float)(__ldcg(Gsrc + i) - mean) : 0.0f;
