@@ -822,6 +822,7 @@ struct FoldArgs {
   double* A;                // KP x KP float64: Gram of the newest iterate (scratch)
   double* G;                // KP x KP float64: Gram of the next extrapolated point (scratch)
   float* Gy;                // KP x KP float32 for the next pass
+  double* bpart;            // [fold blocks][2] block partials of an iteration's fold (||A||^2, sum of G(Y))
 };
 
 // Sums the per-block partials in block order (float64), evaluates the loss of
@@ -867,15 +868,15 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
       // about 48 significant bits), converted to float64 once: float64 adds
       // and conversions per partial saturated B300's narrow float64 pipe
       const float* gp = f.gram_part + src;
-      const size_t st = (size_t)2 * E2 * GR;
+      const size_t pstr = (size_t)2 * E2 * GR;
       float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
       int p = g;
       for (; p + 3 * GR < f.parts; p += 4 * GR) {
         const float* q = gp + (size_t)p * 2 * E2;
         two_sum_acc(h[0], l[0], q[0]);
-        two_sum_acc(h[1], l[1], q[st]);
-        two_sum_acc(h[2], l[2], q[2 * st]);
-        two_sum_acc(h[3], l[3], q[3 * st]);
+        two_sum_acc(h[1], l[1], q[pstr]);
+        two_sum_acc(h[2], l[2], q[2 * pstr]);
+        two_sum_acc(h[3], l[3], q[3 * pstr]);
       }
       for (; p < f.parts; p += GR) two_sum_acc(h[0], l[0], gp[(size_t)p * 2 * E2]);
       s = (((double)h[0] + (double)l[0]) + ((double)h[1] + (double)l[1])) +
@@ -883,11 +884,46 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
     }
     gsum[tid] = s;
     __syncthreads();
+    // an iteration's fold (not an objective-only one) also writes its entries
+    // of the float32 G(Y) for the next pass here, shifted by the previous
+    // pass's mean entry (any constant shift leaves the projection unchanged;
+    // the mean keeps the float32 values small), and block partials of
+    // ||A||_F^2 and of the sum of G(Y)'s entries, from which the last block
+    // forms the loss and the next shift without a pass over the entries
+    double a2 = 0.0, gs = 0.0;
     if (g == 0 && e < nent) {
       double t = gsum[el];
       for (int q = 1; q < GR; ++q) t += gsum[q * EPB + el];
       const int m = e / E2, r = (e % E2) / KP, c = e % KP;
       (m == 0 ? f.A : f.G)[r * KP + c] = t;
+      if (!f.eval) {
+        if (m == 0) {
+          a2 = t * t;
+        } else {
+          const int kk = st->k;
+          const bool in = r < kk && c < kk;
+          gs = in ? t : 0.0;
+          f.Gy[r * KP + c] = in ? (float)(t - st->shift) : 0.0f;
+        }
+      }
+    }
+    if (!f.eval) {
+      __syncthreads();
+      __shared__ double bred[2][256];
+      bred[0][tid] = a2;
+      bred[1][tid] = gs;
+      __syncthreads();
+      for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o) {
+          bred[0][tid] += bred[0][tid + o];
+          bred[1][tid] += bred[1][tid + o];
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        f.bpart[2 * blk] = bred[0][0];
+        f.bpart[2 * blk + 1] = bred[1][0];
+      }
     }
   }
   __threadfence();
@@ -901,9 +937,16 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   __shared__ double red[256];
   const int k = st->k;
   // ||A||_F^2 (fixed-order tree; each thread's entries in four chains, all
-  // loads issued up front: E2 / 256 of them, 64 at k = 128)
+  // loads issued up front: E2 / 256 of them, 64 at k = 128); an iteration's
+  // fold takes it, and the mean of G(Y), from the block partials
   double part = 0.0;
-  {
+  double gmean_part = 0.0;
+  if (!f.eval) {
+    for (int b = tid; b < nblocks; b += 256) {
+      part += __ldcg(f.bpart + 2 * b);
+      gmean_part += __ldcg(f.bpart + 2 * b + 1);
+    }
+  } else {
     constexpr int PT = (E2 + 255) / 256;
     double p4[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -922,6 +965,17 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   }
   const double gram2_new = red[0];
   __syncthreads();
+  double gmean_new = 0.0;
+  if (!f.eval) {
+    red[tid] = gmean_part;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    gmean_new = red[0] / ((double)k * (double)k);
+    __syncthreads();
+  }
   // block sums of the scalar partials: thread t takes partials t, t + 256, ...
   // in order, then a fixed tree (deterministic)
   __shared__ double sred[4][256];
@@ -1004,8 +1058,12 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
     }
   }
   __syncthreads();
-  // float32 G(Y) for the next pass, minus its mean over the k x k block
-  if (!f.eval || f.eval_init) {
+  // float32 G(Y) for the next pass, minus its mean over the k x k block: an
+  // iteration's fold wrote it above (with the previous pass's mean) and here
+  // only keeps this pass's mean for the next one
+  if (!f.eval) {
+    if (tid == 0) st->shift = gmean_new;
+  } else if (f.eval_init) {
     const double* Gsrc = f.eval ? f.A : f.G;
     double msum = 0.0;
     {

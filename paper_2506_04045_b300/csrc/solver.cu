@@ -59,6 +59,7 @@ template <int KP>
 struct KPOps {
   using L = Lay<KP>;
   static int rows_per_tile() { return L::R; }
+  static int fold_nb() { return fold_blocks<KP>(false); }
 
   template <bool MIXED, bool EVAL>
   static cudaError_t setup_pass_attr() {
@@ -231,6 +232,11 @@ static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, boo
   FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
 }
 static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static int kp_fold_blocks(int KP) {
+  int nb = 1;
+  FC_DISPATCH(KP, nb = Ops::fold_nb());
+  return nb;
+}
 static int kp_occ_gram0(int KP) {
   int o = 1;
   FC_DISPATCH(KP, o = Ops::occ_gram0());
@@ -428,7 +434,7 @@ void ctx_free(cluster_ctx* c) {
     if (e) cudaEventDestroy(e);
   void* bufs[] = {c->rp_owned, c->col_owned, c->val_owned, c->val16, c->order, c->cta_pos, c->chunk_ptr,
                   c->chunk_e0, c->chunk_e1, c->hv_part, c->X[0], c->X[1], c->XS[0], c->XS[1], c->Zp, c->A[0],
-                  c->A[1], c->Gy, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work, c->perm, c->inv};
+                  c->A[1], c->Gy, c->bpart, c->gram_part, c->sc_part, c->st, c->Z[0], c->Z[1], c->work, c->perm, c->inv};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -484,6 +490,7 @@ FoldArgs make_fold_args(const cluster_ctx* c, int eval, int eval_init) {
   f.A = c->A[0];
   f.G = c->A[1];
   f.Gy = c->Gy;
+  f.bpart = c->bpart;
   return f;
 }
 
@@ -885,6 +892,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   FC_CUDA(cudaMalloc(&c->A[0], sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->A[1], sizeof(double) * e2));
   FC_CUDA(cudaMalloc(&c->Gy, sizeof(float) * e2));
+  FC_CUDA(cudaMalloc(&c->bpart, sizeof(double) * 2 * (size_t)kp_fold_blocks(c->KP)));
   const int slots = std::max(c->parts, c->parts_upd);
   FC_CUDA(cudaMalloc(&c->gram_part, sizeof(float) * 2 * e2 * slots));
   FC_CUDA(cudaMalloc(&c->sc_part, sizeof(double) * 4 * slots));

@@ -75,6 +75,7 @@ struct cluster_ctx {
   int ovl_blocks[kMaxOvl + 1] = {};
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ovl_ev[kMaxOvl + 1] = {};
+  double* bpart = nullptr;            // fold block partials (fold_kernel of an iteration)
   double* A[2] = {nullptr, nullptr};  // float64 fold scratch: Gram of Xbar^n, Gram of Y^{n+1}
   float* Gy = nullptr;                 // float32 G(Y) (minus its mean) read by the next pass
   float* gram_part = nullptr;
