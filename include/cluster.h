@@ -144,7 +144,7 @@ typedef struct cluster_options {
                           within float32 rounding of 1 and 2, not the same
                           bits); a batch or the overlapped pass uses 2 instead.
                           k <= 16 uses mma.sync (k > 8) or float32 FMA, k > 64
-                          float32 FMA.                                            */
+                          mma.sync.                                               */
   int32_t overlap;     /* 1 = with the internal numbering and n >= 2^20, run the
                           update of each of 8 row chunks on a second stream as
                           soon as the gather has produced that chunk's rows,
