@@ -18,6 +18,14 @@ namespace fc {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Sum over the 32 lanes of a warp by a fixed xor butterfly (every lane gets
+// the same, deterministic result).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
 #ifndef FC_MINB32
 #define FC_MINB32 4  // resident 256-thread blocks per SM the k <= 32 pass is sized for
 #endif

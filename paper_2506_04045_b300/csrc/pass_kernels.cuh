@@ -908,21 +908,25 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
       }
     }
     if (!f.eval) {
-      __syncthreads();
-      __shared__ double bred[2][256];
-      bred[0][tid] = a2;
-      bred[1][tid] = gs;
-      __syncthreads();
-      for (int o = 128; o > 0; o >>= 1) {
-        if (tid < o) {
-          bred[0][tid] += bred[0][tid + o];
-          bred[1][tid] += bred[1][tid + o];
+      // only the group-0 threads (the first EPB / 32 warps) hold entries
+      constexpr int W0 = (EPB + 31) / 32;
+      __shared__ double bred[2][W0];
+      const int warp = tid >> 5, lane = tid & 31;
+      if (warp < W0) {
+        a2 = warp_sum_f64(a2);
+        gs = warp_sum_f64(gs);
+        if (lane == 0) {
+          bred[0][warp] = a2;
+          bred[1][warp] = gs;
         }
-        __syncthreads();
       }
+      __syncthreads();
       if (tid == 0) {
-        f.bpart[2 * blk] = bred[0][0];
-        f.bpart[2 * blk + 1] = bred[1][0];
+        double x = 0.0, y = 0.0;
+#pragma unroll
+        for (int w = 0; w < W0; ++w) x += bred[0][w], y += bred[1][w];
+        f.bpart[2 * blk] = x;
+        f.bpart[2 * blk + 1] = y;
       }
     }
   }
@@ -934,17 +938,19 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   if (!is_last) return;
   __threadfence();
 
-  __shared__ double red[256];
   const int k = st->k;
-  // ||A||_F^2 (fixed-order tree; each thread's entries in four chains, all
-  // loads issued up front: E2 / 256 of them, 64 at k = 128); an iteration's
-  // fold takes it, and the mean of G(Y), from the block partials
-  double part = 0.0;
-  double gmean_part = 0.0;
+  const int warp = tid >> 5, lane = tid & 31;
+  // Six sums, each thread's share in index order (t, t + 256, ...), then a
+  // fixed butterfly across the lanes and the warps in warp order
+  // (deterministic): [0..3] the scalar partials (trace, squared PG norm,
+  // non-finite count, waits given up), [4] ||A||_F^2 (an iteration's fold
+  // takes it from the block partials, an objective-only one from the entries,
+  // in four chains), [5] the sum of G(Y)'s k x k entries (iteration only).
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (!f.eval) {
     for (int b = tid; b < nblocks; b += 256) {
-      part += __ldcg(f.bpart + 2 * b);
-      gmean_part += __ldcg(f.bpart + 2 * b + 1);
+      v[4] += __ldcg(f.bpart + 2 * b);
+      v[5] += __ldcg(f.bpart + 2 * b + 1);
     }
   } else {
     constexpr int PT = (E2 + 255) / 256;
@@ -952,70 +958,58 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
 #pragma unroll
     for (int j = 0; j < PT; ++j) {
       const int i = tid + j * 256;
-      const double v = i < E2 ? __ldcg(f.A + i) : 0.0;
-      p4[j & 3] = fma(v, v, p4[j & 3]);
+      const double x = i < E2 ? __ldcg(f.A + i) : 0.0;
+      p4[j & 3] = fma(x, x, p4[j & 3]);
     }
-    part = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+    v[4] = (p4[0] + p4[1]) + (p4[2] + p4[3]);
   }
-  red[tid] = part;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (tid < o) red[tid] += red[tid + o];
-    __syncthreads();
-  }
-  const double gram2_new = red[0];
-  __syncthreads();
-  double gmean_new = 0.0;
-  if (!f.eval) {
-    red[tid] = gmean_part;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (tid < o) red[tid] += red[tid + o];
-      __syncthreads();
-    }
-    gmean_new = red[0] / ((double)k * (double)k);
-    __syncthreads();
-  }
-  // block sums of the scalar partials: thread t takes partials t, t + 256, ...
-  // in order, then a fixed tree (deterministic)
-  __shared__ double sred[4][256];
   {
-    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-    for (int c = tid; c < f.parts; c += 256) {
-      v0 += __ldcg(f.sc_part + c * 4 + 0);
-      v1 += __ldcg(f.sc_part + c * 4 + 1);
-      v2 += __ldcg(f.sc_part + c * 4 + 2);
-      v3 += __ldcg(f.sc_part + c * 4 + 3);
+    const double2* sp = reinterpret_cast<const double2*>(f.sc_part);  // [parts][2] pairs
+    int c = tid;
+    for (; c + 256 < f.parts; c += 512) {  // two partials' loads in flight
+      const double2 x0 = __ldcg(sp + 2 * c), x1 = __ldcg(sp + 2 * c + 1);
+      const double2 y0 = __ldcg(sp + 2 * (c + 256)), y1 = __ldcg(sp + 2 * (c + 256) + 1);
+      v[0] += x0.x, v[1] += x0.y, v[2] += x1.x, v[3] += x1.y;
+      v[0] += y0.x, v[1] += y0.y, v[2] += y1.x, v[3] += y1.y;
     }
-    sred[0][tid] = v0;
-    sred[1][tid] = v1;
-    sred[2][tid] = v2;
-    sred[3][tid] = v3;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (tid < o)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sred[q][tid] += sred[q][tid + o];
-      __syncthreads();
+    if (c < f.parts) {
+      const double2 x0 = __ldcg(sp + 2 * c), x1 = __ldcg(sp + 2 * c + 1);
+      v[0] += x0.x, v[1] += x0.y, v[2] += x1.x, v[3] += x1.y;
     }
   }
+  __shared__ double wred[6][8];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    v[q] = warp_sum_f64(v[q]);
+    if (lane == 0) wred[q][warp] = v[q];
+  }
+  __syncthreads();
   if (tid == 0) {
-    const double tr = sred[0][0], pg = sred[1][0], bad = sred[2][0], tmo = sred[3][0];
+    double tot[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      double x = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) x += wred[q][w];
+      tot[q] = x;
+    }
+    const double tr = tot[0], pg = tot[1], bad = tot[2], tmo = tot[3], gram2_new = tot[4];
     if (f.eval) {
       st->eval_trace = tr;
       st->eval_gram2 = gram2_new;
       st->eval_f = st->S2 - 2.0 * tr + gram2_new;
       if (f.eval_init) st->gram2_cur = gram2_new;
     } else {
+      // every field this update reads, loaded before any store (one round
+      // trip instead of one per read: a store may alias a later load)
+      const double S2 = st->S2, gram2_cur = st->gram2_cur, tau = st->tau, tol = st->tol;
+      const double loss_prev = st->loss_prev, pg_first_old = st->pg_first, t0 = st->t;
+      const int64_t max_iter = st->max_iter;
+      const int stop_rule = st->stop_rule, accel = st->accel;
       // loss of Xbar^{pass} (= Xbar^{n-1} for this pass n = pass + 1)
-      const double loss = st->S2 - 2.0 * tr + st->gram2_cur;
-      st->trace_last = tr;
-      st->gram2_last = st->gram2_cur;
-      st->loss_last = loss;
-      st->f_iter = pass;
-      const double r = sqrt(pg) / st->tau;
-      st->pg_last = r;
-      if (nnew == 1) st->pg_first = r;
+      const double loss = S2 - 2.0 * tr + gram2_cur;
+      const double r = sqrt(pg) / tau;
+      const double pg_first = nnew == 1 ? r : pg_first_old;
       int done = 0, status = 0;
       int64_t out = nnew;
       if (tmo > 0.0) {
@@ -1028,43 +1022,49 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
         done = 1;
         status = 4;
         out = pass;
-      } else if (st->stop_rule == 0) {
-        if (pass >= 1 && st->loss_prev - loss <= st->tol) {
+      } else if (stop_rule == 0) {
+        if (pass >= 1 && loss_prev - loss <= tol) {
           done = 1;
           out = pass;
         }
-      } else if (st->stop_rule == 1) {
-        if (r <= st->tol * st->pg_first) done = 1;
-      } else if (st->stop_rule == 2) {
-        if (r <= st->tol) done = 1;
+      } else if (stop_rule == 1) {
+        if (r <= tol * pg_first) done = 1;
+      } else if (stop_rule == 2) {
+        if (r <= tol) done = 1;
       }
-      if (!done && nnew >= st->max_iter) {
+      if (!done && nnew >= max_iter) {
         done = 1;
         status = 5;
       }
-      st->loss_prev = loss;
-      st->gram2_cur = gram2_new;
       // t_{n+1}, t_{n+2} and the momentum factors of the next two passes
-      const double t0 = st->t;
       const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t0 * t0));
       const double t2 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t1 * t1));
+      st->trace_last = tr;
+      st->gram2_last = gram2_cur;
+      st->loss_last = loss;
+      st->f_iter = pass;
+      st->pg_last = r;
+      st->pg_first = pg_first;
+      st->loss_prev = loss;
+      st->gram2_cur = gram2_new;
       st->t = t1;
-      st->beta = st->accel ? (t0 - 1.0) / t1 : 0.0;
-      st->beta_next = st->accel ? (t1 - 1.0) / t2 : 0.0;
+      st->beta = accel ? (t0 - 1.0) / t1 : 0.0;
+      st->beta_next = accel ? (t1 - 1.0) / t2 : 0.0;
+      // the mean of G(Y)'s entries: the shift of the next pass's float32 G(Y)
+      st->shift = tot[5] / ((double)k * (double)k);
       st->out_iter = out;
       st->status = status;
       st->done = done;
       st->pass = nnew;
     }
   }
-  __syncthreads();
   // float32 G(Y) for the next pass, minus its mean over the k x k block: an
-  // iteration's fold wrote it above (with the previous pass's mean) and here
-  // only keeps this pass's mean for the next one
-  if (!f.eval) {
-    if (tid == 0) st->shift = gmean_new;
-  } else if (f.eval_init) {
-    const double* Gsrc = f.eval ? f.A : f.G;
+  // iteration's fold wrote it above (with the previous pass's mean) and its
+  // last block only keeps this pass's mean for the next one (above); the
+  // start's objective-only fold writes it here
+  if (f.eval && f.eval_init) {
+    __shared__ double red[256];
+    const double* Gsrc = f.A;
     double msum = 0.0;
     {
       constexpr int PT = (E2 + 255) / 256;

@@ -83,18 +83,17 @@ struct KPOps {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fista_pass_kernel<KP, false, false>, L::NT, smem);
     return occ < 1 ? 1 : occ;
   }
-  static void launch_pass(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
+  static void launch_pass(const PassArgs& a, int grid, bool mixed, cudaStream_t s, const LaunchOpt& o) {
     const size_t smem = pass_smem_bytes<KP>(false);
-    if (mixed) fista_pass_kernel<KP, true, false><<<grid, L::NT, smem, s>>>(a);
-    else fista_pass_kernel<KP, false, false><<<grid, L::NT, smem, s>>>(a);
+    launch_ex(mixed ? fista_pass_kernel<KP, true, false> : fista_pass_kernel<KP, false, false>, grid, L::NT, smem, s,
+              o, a);
   }
   static void launch_eval(const PassArgs& a, int grid, cudaStream_t s) {
     fista_pass_kernel<KP, false, true><<<grid, L::NT, pass_smem_bytes<KP>(true), s>>>(a);
   }
-  static void launch_heavy(const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s) {
-    if (eval) heavy_kernel<KP, false, true><<<grid, L::NT, 0, s>>>(a);
-    else if (mixed) heavy_kernel<KP, true, false><<<grid, L::NT, 0, s>>>(a);
-    else heavy_kernel<KP, false, false><<<grid, L::NT, 0, s>>>(a);
+  static void launch_heavy(const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s, const LaunchOpt& o) {
+    launch_ex(eval ? heavy_kernel<KP, false, true> : mixed ? heavy_kernel<KP, true, false> : heavy_kernel<KP, false, false>,
+              grid, L::NT, 0, s, o, a);
   }
   // first gather unit whose rows all lie at positions >= r (units: chunk units
   // of hub rows, then row units of TPW * kRowsPerUnit positions from n_heavy)
@@ -104,7 +103,9 @@ struct KPOps {
     const int64_t q = std::max<int64_t>(r, n_heavy) - n_heavy;
     return cu + (q + per - 1) / per;
   }
-  static int64_t units(bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks) {
+  static int64_t units(bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks, int rpu) {
+    if (rpu == 1)
+      return mixed ? spmm_units<KP, true, 1>(n, n_heavy, n_chunks) : spmm_units<KP, false, 1>(n, n_heavy, n_chunks);
     return mixed ? spmm_units<KP, true>(n, n_heavy, n_chunks) : spmm_units<KP, false>(n, n_heavy, n_chunks);
   }
   static int occ_spmm(bool mixed) {
@@ -141,46 +142,27 @@ struct KPOps {
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(update_kernel<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
-  static void launch_spmm(const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-    if (mixed) spmm_kernel<KP, true><<<grid, L::NT, 0, s>>>(a);
-    else spmm_kernel<KP, false><<<grid, L::NT, 0, s>>>(a);
+  // o.win_bytes > 0: with a persisting L2 window (the gathered iterate's hot rows)
+  // rpu: rows per team per gather unit (kRowsPerUnit or 1)
+  static void launch_spmm(const PassArgs& a, int grid, bool mixed, int rpu, cudaStream_t s, const LaunchOpt& o) {
+    if (rpu == 1) launch_ex(mixed ? spmm_kernel<KP, true, 1> : spmm_kernel<KP, false, 1>, grid, L::NT, 0, s, o, a);
+    else launch_ex(mixed ? spmm_kernel<KP, true> : spmm_kernel<KP, false>, grid, L::NT, 0, s, o, a);
   }
-  // the same launch with a persisting L2 window over [base, base + bytes)
-  static void launch_spmm_window(const PassArgs& a, int grid, bool mixed, cudaStream_t s, void* base, size_t bytes) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(L::NT);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    at[0].val.accessPolicyWindow.base_ptr = base;
-    at[0].val.accessPolicyWindow.num_bytes = bytes;
-    at[0].val.accessPolicyWindow.hitRatio = 1.0f;
-    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (mixed) cudaLaunchKernelEx(&cfg, spmm_kernel<KP, true>, a);
-    else cudaLaunchKernelEx(&cfg, spmm_kernel<KP, false>, a);
-  }
-  static void launch_finalize(const PassArgs& a, cudaStream_t s) {
+  static void launch_finalize(const PassArgs& a, cudaStream_t s, const LaunchOpt& o) {
     const int64_t threads = a.n_heavy * L::T;
     int grid = (int)std::min<int64_t>((threads + 255) / 256, 4096);
-    heavy_finalize_kernel<KP><<<grid < 1 ? 1 : grid, 256, 0, s>>>(a);
+    launch_ex(heavy_finalize_kernel<KP>, grid < 1 ? 1 : grid, 256, 0, s, o, a);
   }
-  static void launch_update(const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s) {
+  static void launch_update(const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s, const LaunchOpt& o) {
     if constexpr (TcUpd<KP>::ON) {
       if (tc) {
-        const size_t smem = TcUpd<KP>::smem();
-        if (mixed) update_tc_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
-        else update_tc_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
+        launch_ex(mixed ? update_tc_kernel<KP, true> : update_tc_kernel<KP, false>, grid, L::NT, TcUpd<KP>::smem(), s,
+                  o, a);
         return;
       }
     }
-    const size_t smem = update_smem_bytes<KP>();
-    if (mixed) update_kernel<KP, true><<<grid, L::NT, smem, s>>>(a);
-    else update_kernel<KP, false><<<grid, L::NT, smem, s>>>(a);
+    launch_ex(mixed ? update_kernel<KP, true> : update_kernel<KP, false>, grid, L::NT, update_smem_bytes<KP>(), s, o,
+              a);
   }
   static void launch_gram0(const float* X, int64_t n, float* gp, double* sp, int grid, cudaStream_t s) {
     if constexpr (KP <= 64) gram0_kernel<KP><<<grid, 256, 0, s>>>(X, n, gp, sp);
@@ -190,9 +172,9 @@ struct KPOps {
     if constexpr (KP <= 64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram0_kernel<KP>, 256, 0);
     return occ < 1 ? 1 : occ;
   }
-  static void launch_fold(const FoldArgs& f, cudaStream_t s) {
+  static void launch_fold(const FoldArgs& f, cudaStream_t s, const LaunchOpt& o) {
     const int nent = f.eval ? KP * KP : 2 * KP * KP;
-    fold_kernel<KP><<<(nent + fold_epb<KP>() - 1) / fold_epb<KP>(), 256, 0, s>>>(f);
+    launch_ex(fold_kernel<KP>, (nent + fold_epb<KP>() - 1) / fold_epb<KP>(), 256, 0, s, o, f);
   }
 };
 
@@ -222,16 +204,20 @@ static int kp_occupancy(int KP, bool mixed) {
   FC_DISPATCH(KP, o = Ops::occupancy(mixed));
   return o;
 }
-static void kp_launch_pass(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_pass(a, grid, mixed, s));
+static void kp_launch_pass(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s,
+                           const LaunchOpt& o = LaunchOpt()) {
+  FC_DISPATCH(KP, Ops::launch_pass(a, grid, mixed, s, o));
 }
 static void kp_launch_eval(int KP, const PassArgs& a, int grid, cudaStream_t s) {
   FC_DISPATCH(KP, Ops::launch_eval(a, grid, s));
 }
-static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s));
+static void kp_launch_heavy(int KP, const PassArgs& a, int grid, bool mixed, bool eval, cudaStream_t s,
+                            const LaunchOpt& o = LaunchOpt()) {
+  FC_DISPATCH(KP, Ops::launch_heavy(a, grid, mixed, eval, s, o));
 }
-static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_fold(f, s)); }
+static void kp_launch_fold(int KP, const FoldArgs& f, cudaStream_t s, const LaunchOpt& o = LaunchOpt()) {
+  FC_DISPATCH(KP, Ops::launch_fold(f, s, o));
+}
 static int kp_fold_blocks(int KP) {
   int nb = 1;
   FC_DISPATCH(KP, nb = Ops::fold_nb());
@@ -250,9 +236,9 @@ static int64_t kp_unit_of_position(int KP, bool mixed, int64_t r, int64_t n_heav
   FC_DISPATCH(KP, u = Ops::unit_of_position(mixed, r, n_heavy, n_chunks));
   return u;
 }
-static int64_t kp_units(int KP, bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks) {
+static int64_t kp_units(int KP, bool mixed, int64_t n, int64_t n_heavy, int64_t n_chunks, int rpu = kRowsPerUnit) {
   int64_t u = 0;
-  FC_DISPATCH(KP, u = Ops::units(mixed, n, n_heavy, n_chunks));
+  FC_DISPATCH(KP, u = Ops::units(mixed, n, n_heavy, n_chunks, rpu));
   return u;
 }
 static int kp_occ_spmm(int KP, bool mixed) {
@@ -270,16 +256,16 @@ static cudaError_t kp_setup_update_attr(int KP) {
   FC_DISPATCH(KP, e = Ops::setup_update_attr());
   return e;
 }
-static void kp_launch_spmm(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_spmm(a, grid, mixed, s));
+static void kp_launch_spmm(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s,
+                           const LaunchOpt& o = LaunchOpt(), int rpu = kRowsPerUnit) {
+  FC_DISPATCH(KP, Ops::launch_spmm(a, grid, mixed, rpu, s, o));
 }
-static void kp_launch_finalize(int KP, const PassArgs& a, cudaStream_t s) { FC_DISPATCH(KP, Ops::launch_finalize(a, s)); }
-static void kp_launch_spmm_window(int KP, const PassArgs& a, int grid, bool mixed, cudaStream_t s, void* base,
-                                  size_t bytes) {
-  FC_DISPATCH(KP, Ops::launch_spmm_window(a, grid, mixed, s, base, bytes));
+static void kp_launch_finalize(int KP, const PassArgs& a, cudaStream_t s, const LaunchOpt& o = LaunchOpt()) {
+  FC_DISPATCH(KP, Ops::launch_finalize(a, s, o));
 }
-static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s) {
-  FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, tc, s));
+static void kp_launch_update(int KP, const PassArgs& a, int grid, bool mixed, bool tc, cudaStream_t s,
+                             const LaunchOpt& o = LaunchOpt()) {
+  FC_DISPATCH(KP, Ops::launch_update(a, grid, mixed, tc, s, o));
 }
 
 // ---- streaming update (tc_stream.cuh) ----
@@ -333,18 +319,15 @@ static cluster_status make_stream_maps(cluster_ctx* c) {
 }
 
 // the row-local update of a split pass with the context's engine
-static void launch_update_ctx(const cluster_ctx* c, const PassArgs& a, cudaStream_t s) {
+static void launch_update_ctx(const cluster_ctx* c, const PassArgs& a, cudaStream_t s,
+                              const LaunchOpt& o = LaunchOpt()) {
   if (c->stream_update) {
     const bool full = c->k == 32;
-    if (c->mixed) {
-      if (full) update_stream_kernel<true, true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
-      else update_stream_kernel<true, false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
-    } else {
-      if (full) update_stream_kernel<false, true><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
-      else update_stream_kernel<false, false><<<c->stream_grid, ts::NT, ts::SMEM, s>>>(a, *c->smaps);
-    }
+    auto fn = c->mixed ? (full ? update_stream_kernel<true, true> : update_stream_kernel<true, false>)
+                       : (full ? update_stream_kernel<false, true> : update_stream_kernel<false, false>);
+    launch_ex(fn, c->stream_grid, ts::NT, ts::SMEM, s, o, a, *c->smaps);
   } else {
-    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s);
+    kp_launch_update(c->KP, a, c->parts_upd, c->mixed, c->tc_update, s, o);
   }
 }
 
@@ -510,8 +493,10 @@ static void enqueue_split_ovl(const cluster_ctx* c, cudaStream_t s, int parity, 
     g.unit_hi = c->ovl_units[ch + 1];
     g.work = c->work + ch;
     if (g.unit_hi > g.unit_lo) {
-      if (c->l2_window_bytes) kp_launch_spmm_window(c->KP, g, c->spmm_grid_ovl, c->mixed, s, win, c->l2_window_bytes);
-      else kp_launch_spmm(c->KP, g, c->spmm_grid_ovl, c->mixed, s);
+      LaunchOpt o;
+      o.win = win;
+      o.win_bytes = c->l2_window_bytes;
+      kp_launch_spmm(c->KP, g, c->spmm_grid_ovl, c->mixed, s, o);
     }
     if (ch == 0 && c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
     if (tev && ch + 1 == c->ovl) {
@@ -536,11 +521,10 @@ static void enqueue_pass(const cluster_ctx* c, cudaStream_t s, int parity) {
   if (c->split && c->ovl > 0) {
     enqueue_split_ovl(c, s, parity, nullptr);
   } else if (c->split) {
-    if (c->l2_window_bytes)
-      kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
-                            c->mixed ? (void*)c->XS[parity & 1] : (void*)c->X[parity & 1], c->l2_window_bytes);
-    else
-      kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+    LaunchOpt g;
+    g.win = c->mixed ? (void*)c->XS[parity & 1] : (void*)c->X[parity & 1];
+    g.win_bytes = c->l2_window_bytes;
+    kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s, g, c->spmm_rpu);
     if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
     launch_update_ctx(c, a, s);
   } else {
@@ -826,6 +810,18 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   }
   c->row_cost = 6;
   FC_TRY(build_schedule(c));
+  // An instance whose units of kRowsPerUnit rows per team leave resident warps
+  // idle gathers in one-row units instead (shorter chains of dependent loads
+  // per unit; same sums).  A gather launch then needs no more warps (8 a
+  // block) than units: a surplus warp only draws a unit number from the shared
+  // counter and stops, and at a few thousand rows those draws (one counter)
+  // took longer than the gather.
+  if (c->split) {
+    const int64_t u4 = kp_units(c->KP, c->mixed, n, c->n_heavy, c->n_chunks);
+    c->spmm_rpu = (u4 < (int64_t)c->spmm_grid * 8 && n < kOvlMinRows) ? 1 : kRowsPerUnit;
+    const int64_t units = c->spmm_rpu == 1 ? kp_units(c->KP, c->mixed, n, c->n_heavy, c->n_chunks, 1) : u4;
+    c->spmm_grid = (int)std::min<int64_t>(c->spmm_grid, std::max<int64_t>(1, (units + 7) / 8));
+  }
 
   // Overlapped pass: with the internal numbering the gather order is the
   // identity, so a prefix of the gather's units is a prefix of the rows and
@@ -1142,11 +1138,10 @@ extern "C" cluster_status cluster_enqueue_profiled(cluster_ctx* c, int64_t iters
       enqueue_split_ovl(c, s, (int)((c->pass_guess + i) & 1), &e[1]);
     } else if (c->split) {
       const int par = (int)((c->pass_guess + i) & 1);
-      if (c->l2_window_bytes)
-        kp_launch_spmm_window(c->KP, a, c->spmm_grid, c->mixed, s,
-                              c->mixed ? (void*)c->XS[par] : (void*)c->X[par], c->l2_window_bytes);
-      else
-        kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s);
+      LaunchOpt g;
+      g.win = c->mixed ? (void*)c->XS[par] : (void*)c->X[par];
+      g.win_bytes = c->l2_window_bytes;
+      kp_launch_spmm(c->KP, a, c->spmm_grid, c->mixed, s, g, c->spmm_rpu);
       cudaEventRecord(e[1], s);
       if (c->n_heavy > 0) kp_launch_finalize(c->KP, a, s);
       cudaEventRecord(e[2], s);

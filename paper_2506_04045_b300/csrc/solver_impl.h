@@ -62,6 +62,7 @@ struct cluster_ctx {
   int stream_grid = 0;
   fc::StreamMaps* smaps = nullptr;
   int spmm_grid = 1;
+  int spmm_rpu = 4;                     // rows per team per gather unit (4 or 1)
   // overlapped pass (opt.overlap): row chunk c's update runs on side_stream
   // once the gather units that cover its rows (ovl_units[c+1]) are done, while
   // the next chunks are gathered; the update blocks and partial slots are the

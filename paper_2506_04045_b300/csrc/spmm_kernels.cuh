@@ -81,20 +81,24 @@ __host__ __device__ constexpr int spmm_min_blocks() {
   return (KP == 32 && !MIXED) ? 5 : 0;
 }
 
-template <int KP, bool MIXED>
+// RPU rows per team per unit: kRowsPerUnit, or 1 for an instance too small to
+// give every resident warp a unit of kRowsPerUnit rows (a unit's rows are
+// gathered one after another, so at a few thousand rows the last unit's chain
+// of dependent loads sets the launch's time).
+template <int KP, bool MIXED, int RPU = kRowsPerUnit>
 __global__ void __launch_bounds__(Lay<KP>::NT, spmm_min_blocks<KP, MIXED>()) spmm_kernel(PassArgs a) {
   volatile FistaState* vs = a.st;
   if (vs->done || vs->pass >= vs->limit) return;
   const int64_t pass = vs->pass;
   const int lane = threadIdx.x & 31;
-  const int64_t units = a.unit_hi < 0 ? spmm_units<KP, MIXED>(a.n, a.n_heavy, a.n_chunks) : a.unit_hi;
+  const int64_t units = a.unit_hi < 0 ? spmm_units<KP, MIXED, RPU>(a.n, a.n_heavy, a.n_chunks) : a.unit_hi;
   for (;;) {
     unsigned long long u = 0;
     if (lane == 0) u = atomicAdd(a.work, 1ull);
     u = __shfl_sync(kFull, u, 0);
     const int64_t unit = a.unit_lo + (int64_t)u;
     if (unit >= units) break;
-    spmm_unit<KP, MIXED>(a, pass, unit, lane);
+    spmm_unit<KP, MIXED, 0, RPU>(a, pass, unit, lane);
   }
 }
 
