@@ -131,9 +131,9 @@ typedef struct cluster_options {
                           0 = no window.  A cache hint: no value changes.       */
   int32_t update_engine; /* form of the row-local update for 17 <= k <= 64:
                           0 = automatic (default): k <= 32 streams (3) on a
-                          solver of at least 2^17 articles and uses 2 otherwise
-                          (batched and served instances too); 33 <= k <= 64
-                          uses 1 (measured faster there);
+                          solver of at least 2^17 articles; everything else
+                          (smaller solvers, batched and served instances,
+                          33 <= k <= 64) uses 1 (measured faster there);
                           1 = warp-level mma.sync, blocks of rows;
                           2 = tcgen05.mma with TMEM accumulators, the same
                           blocks, products and order as 1 (the same bits);
@@ -303,9 +303,11 @@ CLUSTER_API cluster_status cluster_state_size(cluster_ctx* ctx, size_t* bytes);
 CLUSTER_API cluster_status cluster_get_state(cluster_ctx* ctx, void* host_buf, size_t bytes);
 CLUSTER_API cluster_status cluster_set_state(cluster_ctx* ctx, const void* host_buf, size_t bytes);
 
-/* Test hook for the timeout path.  flags bit 0: the tcgen05 update (k in
- * 17..32 with update_engine 0) still issues its y G products but withholds
- * the commit that signals their completion, so its bounded waits give up
+/* Test hook for the timeout path.  flags bit 0: the tcgen05 updates (k in
+ * 17..32 with update_engine 2, and the streaming update: update_engine 3, or
+ * 0 on a solver of at least 2^17 articles) still issue their y G products but
+ * withhold
+ * the commit that signals their completion, so their bounded waits give up
  * after about one second; the run then ends with report status
  * CLUSTER_ETIMEOUT, out_iter names the last complete iterate and the context
  * stays usable (report, U, checkpoint).  flags 0 restores normal operation.

@@ -79,6 +79,14 @@ struct BOps {
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, upd_fn(bc.mixed, false), L::NT, smem);
     bc.occ_spmm = std::max(1, o1);
     bc.occ_upd = std::max(1, o2);
+    // untuned default: a class whose units of kRowsPerUnit rows per team leave
+    // resident gather warps idle takes one-row units (shape 1; shorter chains
+    // of dependent loads per unit, the same sums)
+    if (!bc.tuned && bc.units_s[0] < (int64_t)sms * bc.occ_spmm * L::WARPS) {
+      bc.shape = 1;
+      bc.units = bc.units_s[1];
+      bc.d_unit_base = bc.d_ub[1];
+    }
     bc.spmm_grid = sms * std::max(1, o1);
     bc.gather_blocks_max = std::max<int64_t>(1, (bc.units + L::WARPS - 1) / L::WARPS);
     bc.spmm_grid = (int)std::min<int64_t>(bc.spmm_grid, bc.gather_blocks_max);

@@ -773,10 +773,13 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->heavy_grid = sms * occ;
   c->split = opt.fused_pass == 0;
   // tcgen05 per-block update: engine 2 (and 3 where the streaming form does
-  // not apply) for k in 17..64; engine 0 for k in 17..32 only (for k in
-  // 33..64 the warp form measured faster: 2.9 vs 3.2 ms per batched iteration
-  // of the k = 64 class, the 16-row tiles being latency-bound)
-  c->tc_update = opt.update_engine == 2 || opt.update_engine == 3 || (opt.update_engine == 0 && c->KP <= 32);
+  // not apply) for k in 17..64.  Engine 0 takes the warp form wherever it does
+  // not stream: its 16-row tiles keep more rows in flight per SM than the
+  // per-block tcgen05 kernel's chain of short MMA round trips (per iteration,
+  // k = 32: 47.1 vs 52.1 us at n = 20,000, 66.0 vs 78.4 us at n = 60,000;
+  // k = 64 class of the batched workload: 2.9 vs 3.2 ms; the k = 32 class:
+  // 1.10 vs 1.13 ms)
+  c->tc_update = opt.update_engine == 2 || opt.update_engine == 3;
   // streaming update for 17 <= k <= 32 on a solo split solver without the
   // overlapped pass: engine 0 from kStreamMinRows articles, engine 3 always
   c->stream_update = c->split && capture && c->KP == 32 && !opt.overlap &&

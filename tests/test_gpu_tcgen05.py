@@ -40,7 +40,7 @@ def test_tcgen05_update_equals_warp_update_bitwise(k, precision):
     spec = synth.GraphSpec("dcsbm", 30011, k, 70 + k, mean_deg=25.0)
     rp, c, v = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(spec.n, k, 70 + k, device="cuda")
-    Ut, rt = _run(rp, c, v, U0, 25, precision=precision, update_engine=0)
+    Ut, rt = _run(rp, c, v, U0, 25, precision=precision, update_engine=2)
     Uw, rw = _run(rp, c, v, U0, 25, precision=precision, update_engine=1)
     assert rt["iters"] == rw["iters"] == 25
     assert torch.equal(Ut, Uw)
@@ -62,9 +62,9 @@ def test_tcgen05_update_in_a_batch_equals_solo():
         rp, c, v = synth.make_graph(sp)
         U0 = synth.dirichlet_u0(sp.n, sp.k, sp.seed)
         inst.append(tuple(t.cuda().contiguous() for t in (rp, c, v, U0)))
-    # batch engine, solo engine: tcgen05 (k <= 32) vs warp, warp vs tcgen05,
-    # tcgen05 for every k in 17..64 vs warp
-    for eng_b, eng_s in ((0, 1), (1, 0), (2, 1)):
+    # batch engine, solo engine: automatic (the warp form here) vs tcgen05,
+    # warp vs tcgen05, tcgen05 for every k in 17..64 vs warp
+    for eng_b, eng_s in ((0, 2), (1, 2), (2, 1)):
         b = pkg.Batch(inst, stop_rule=pkg.STOP_NONE, max_iter=20, update_engine=eng_b)
         b.step(20)
         for i, (rp, c, v, U0) in enumerate(inst):
@@ -77,7 +77,7 @@ def test_wait_that_gives_up_is_a_status_and_the_context_survives():
     spec = synth.GraphSpec("dcsbm", 5000, 32, 91, mean_deg=20.0)
     rp, c, v = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(spec.n, 32, 91, device="cuda")
-    s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50)
+    s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50, update_engine=2)
     s.step(3)
     U3 = s.get_U().clone()
     s.test_hooks(1)
@@ -92,7 +92,7 @@ def test_wait_that_gives_up_is_a_status_and_the_context_survives():
     s.test_hooks(0)
     s.close()
     # the device is still fine for the next context: the same three iterations, the same bits
-    s2 = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50)
+    s2 = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_NONE, max_iter=50, update_engine=2)
     s2.step(3)
     assert torch.equal(s2.get_U(), U3)
     s2.close()
@@ -105,7 +105,7 @@ def test_tcgen05_update_small_and_ragged_n(n):
     spec = synth.GraphSpec("dcsbm", n, 32, 300 + n, mean_deg=min(12.0, n / 2.0))
     rp, c, v = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(n, 32, 300 + n, device="cuda")
-    Ut, rt = _run(rp, c, v, U0, 30, update_engine=0)
+    Ut, rt = _run(rp, c, v, U0, 30, update_engine=2)
     Uw, rw = _run(rp, c, v, U0, 30, update_engine=1)
     assert torch.equal(Ut, Uw)
     assert rt["f"] == rw["f"] and rt["pg_norm"] == rw["pg_norm"]
@@ -125,7 +125,7 @@ def test_tcgen05_update_with_a_stop_rule_inside_a_graph():
     rp, c, v = synth.make_graph(spec, device="cuda")
     U0 = synth.dirichlet_u0(spec.n, 20, 333, device="cuda")
     outs = []
-    for eng in (0, 1):
+    for eng in (2, 1):
         s = pkg.Solver(rp, c, v, U0, stop_rule=pkg.STOP_PG_REL, tol=0.5, max_iter=400, update_engine=eng)
         rep = s.solve()
         outs.append((s.get_U(), rep))
