@@ -112,16 +112,20 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint
 // row-major fragment reads conflict-free, TSB (= 8 mod 16) the transposed
 // Gram reads and the float2 stores of Y G.
 //
-// KP = 128 (the update only, not the objective-only pass): the same Y G; the
-// Gram blocks are only those on or above the diagonal (16 x 8 blocks
-// (mi, nj) with nj >= 2 mi: the fold reads the upper triangle), TRIB per
-// matrix, spread evenly over the warps (TPW_B per warp, in (matrix, mi, nj)
-// order, so a warp's A fragment changes at most once or twice): the full
-// square would need 16 blocks of accumulators per warp, beyond the register
-// budget of a 512-thread block.
+// KP = 64 and 128 (the update only, not the objective-only pass): the same
+// Y G; the Gram blocks are only those on or above the diagonal (16 x 8
+// blocks (mi, nj) with nj >= 2 mi: the fold reads the upper triangle), TRIB
+// per matrix, spread evenly over the warps (TPW_B per warp, in (matrix, mi,
+// nj) order, so a warp's A fragment changes at most once or twice).  Each
+// block's products and their order are those of the full square, so the
+// entries the fold reads keep their bits; at KP = 64 the triangle is 40 of
+// the square's 64 blocks, at KP = 128 the square would need 16 blocks of
+// accumulators per warp, beyond the register budget of a 512-thread block.
+// KP = 128 also splits Y G's 16 K steps into two accumulation chains (YG2).
 template <int KP, bool EVAL>
 struct MmaLay {
-  static constexpr bool TRI = KP == 128 && !EVAL;
+  static constexpr bool TRI = (KP == 64 || KP == 128) && !EVAL;
+  static constexpr bool YG2 = KP == 128 && !EVAL;
   static constexpr bool ON = (KP >= 16 && KP <= 64) || TRI;
   static constexpr int TSA = KP + 4;
   static constexpr int TSB = KP + 8;
@@ -464,9 +468,9 @@ __device__ __forceinline__ void pass_range(const PassArgs& a, int64_t pass, int6
           const uint32_t al[4] = {yl[8 * ks], yl[8 * M::TSA + 8 * ks], yl[8 * ks + 4], yl[8 * M::TSA + 8 * ks + 4]};
           const uint4 g = Gf[(yn * M::KS + ks) * 32 + lane];
           const uint32_t bh[2] = {g.x, g.y}, bl[2] = {g.z, g.w};
-          mma3_tf32((M::TRI && (ks & 1)) ? dq2 : dq, ah, al, bh, bl);
+          mma3_tf32((M::YG2 && (ks & 1)) ? dq2 : dq, ah, al, bh, bl);
         }
-        if constexpr (M::TRI) {
+        if constexpr (M::YG2) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) dq[q] += dq2[q];
         }
