@@ -512,7 +512,7 @@ def run_native(args, ws, rank, local):
         kname = f"fista_pass_kernel<32,{tag},false>"
     else:
         b_pass = gather_bytes(n, nnz, k, mixed)
-        kname = f"spmm_kernel<32,{tag}>"
+        kname = f"spmm_kernel<32,{tag},4>"
     achieved = b_pass / (kt["pass_ms"] / 1000.0) / 1e9
     traffic = traffic_for(head + ("_fused" if args.fused else ""),
                           f"dcsbm n={n} k={k} nnz={nnz} seed={args.seed}")
