@@ -266,11 +266,12 @@ CLUSTER_API cluster_status cluster_objective(const cluster_csr* S, int32_t k, co
  * (index64 = 1), n < 2^31.  Rows are split evenly over the GPU rather than
  * ordered by degree, so graphs with rows of very high degree run slower than
  * with cluster_objective.
- * The first call on a device looks up the scratch array's device address for
- * that device (cudaGetSymbolAddress) and keeps it for the life of the
- * process; make that first call before any stream capture, and do not use
- * the library across a cudaDeviceReset (the module is reloaded and the kept
- * address goes stale).  All calls share the one array and each call resets
+ * The call cannot be part of a stream capture (it synchronises `stream` and
+ * reads partial sums on the host): on a capturing stream it returns EINVAL
+ * and enqueues nothing.  The first call on a device looks up the scratch
+ * array's device address for that device (cudaGetSymbolAddress) and keeps it
+ * for the life of the process; do not use the library across a
+ * cudaDeviceReset (the module is reloaded and the kept address goes stale).  All calls share the one array and each call resets
  * what must start at zero, so calls that overlap on the GPU (other threads,
  * other streams) race and must be serialised by the caller.  S is trusted as
  * in cluster_objective (not validated).  The call synchronises `stream` and

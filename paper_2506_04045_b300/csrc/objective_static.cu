@@ -163,6 +163,13 @@ extern "C" cluster_status cluster_objective_static(const cluster_csr* S, int32_t
     FC_EINVAL("cluster_objective_static: k must be 2, 4, 8, 16 or 32 (got %d); other k need a padded copy of U", k);
   if (reinterpret_cast<uintptr_t>(U) % (k == 2 ? 8 : 16) != 0)
     FC_EINVAL("cluster_objective_static: U must be %d-byte aligned", k == 2 ? 8 : 16);
+  // the call synchronises its stream and reads partial sums on the host, which
+  // a stream capture cannot record
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FC_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    FC_EINVAL("cluster_objective_static: the stream is being captured (the call synchronises it and reads "
+              "results on the host, so it cannot be part of a CUDA graph)");
   int dev = 0;
   FC_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) FC_EINVAL("cluster_objective_static: device index %d out of range", dev);

@@ -77,3 +77,23 @@ def test_static_objective_rejects_what_it_cannot_do_without_memory():
     assert ei.value.status == pkg.EINVAL and "int64" in str(ei.value)
     f = pkg.objective_static(rp, c, v, U4)
     assert abs(f - pkg.objective(rp, c, v, U4)) <= TOL_F * abs(f)
+
+
+def test_static_objective_refuses_a_capturing_stream():
+    # it synchronises its stream and reads partials on the host: on a stream
+    # under capture it returns EINVAL before enqueuing anything, and the
+    # capture itself stays valid
+    spec = synth.GraphSpec("dcsbm", 2000, 4, 8, mean_deg=10.0)
+    rp, c, v = [t.cuda() for t in synth.make_graph(spec)]
+    U4 = synth.dirichlet_u0(spec.n, 4, 8).cuda()
+    f0 = pkg.objective_static(rp, c, v, U4)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        with pytest.raises(pkg.ClusterError) as ei:
+            pkg.objective_static(rp, c, v, U4, stream=s)
+        U4.add_(0.0)   # the capture still records work
+    assert ei.value.status == pkg.EINVAL and "captured" in str(ei.value)
+    g.replay()
+    torch.cuda.synchronize()
+    assert pkg.objective_static(rp, c, v, U4) == f0
