@@ -35,11 +35,6 @@ __device__ __forceinline__ int find_segment(const int64_t* base, int m, int64_t 
   return lo;
 }
 
-__device__ __forceinline__ bool instance_idle(const FistaState* st) {
-  const volatile FistaState* vs = st;
-  return vs->done || vs->pass >= vs->limit;
-}
-
 // Gather tile shapes the batch autotuner chooses from, per class: nonzeros per
 // batch per row (NB) and rows per team per work unit (RPU).  Shape 0 is the
 // solo solver's; 1 takes single-row units (finer dynamic balance over many
@@ -64,8 +59,8 @@ __global__ void __launch_bounds__(Lay<KP>::NT) batch_spmm_kernel(BatchMeta b) {
     if ((int64_t)u >= total) break;
     const int j = find_segment(b.unit_base, b.m, (int64_t)u);
     const PassArgs& a = b.args[j];
-    if (instance_idle(a.st)) continue;
-    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+    const int64_t pass = pass_to_run(a.st);
+    if (pass < 0) continue;
     spmm_unit<KP, MIXED, BShape<KP, MIXED, S>::NB, BShape<KP, MIXED, S>::RPU>(a, pass, (int64_t)u - b.unit_base[j],
                                                                              lane);
   }
@@ -80,8 +75,8 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(BatchMeta b) {
   for (int64_t h = t / L::T; h < total; h += teams) {
     const int j = find_segment(b.heavy_base, b.m, h);
     const PassArgs& a = b.args[j];
-    if (instance_idle(a.st)) continue;
-    const int64_t pass = ((const volatile FistaState*)a.st)->pass;
+    const int64_t pass = pass_to_run(a.st);
+    if (pass < 0) continue;
     finalize_row<KP>(a, pass, h - b.heavy_base[j], (int)(t % L::T));
   }
 }
@@ -99,9 +94,9 @@ __device__ __forceinline__ bool next_update_item(const BatchMeta& b, int& item_s
   const int j = b.item_inst[item];
   slot = b.item_slot[item];
   a = &b.args[j];
-  idle = instance_idle(a->st);
+  pass = pass_to_run(a->st);
+  idle = pass < 0;
   if (idle) return true;
-  pass = ((const volatile FistaState*)a->st)->pass;
   const int parts = b.parts_upd[j];
   p0 = a->n * (int64_t)slot / parts;
   p1 = a->n * (int64_t)(slot + 1) / parts;

@@ -45,6 +45,17 @@ struct Lay {
   static constexpr int MINB = KP <= 4 ? 2 : (KP == 8 ? 3 : (KP == 16 ? 4 : (KP == 32 ? FC_MINB32 : (KP == 64 ? 2 : 1))));
 };
 
+// The pass a kernel of the iteration runs, or -1 when the solve is done or
+// past its step limit.  The three fields are read together (independent
+// volatile loads: one round trip to L2 instead of one per field).
+__device__ __forceinline__ int64_t pass_to_run(const FistaState* st) {
+  const volatile FistaState* vs = st;
+  const int32_t done = vs->done;
+  const int64_t pass = vs->pass;
+  const int64_t limit = vs->limit;
+  return (done != 0 || pass >= limit) ? -1 : pass;
+}
+
 struct PassArgs {
   const int64_t* row_ptr;    // [n+1]
   const int32_t* col;        // [nnz]

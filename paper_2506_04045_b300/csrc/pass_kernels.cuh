@@ -741,9 +741,8 @@ template <int KP, bool MIXED, bool EVAL>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(PassArgs a) {
   int64_t pass;
   if constexpr (!EVAL) {
-    volatile FistaState* vs = a.st;
-    if (vs->done || vs->pass >= vs->limit) return;
-    pass = vs->pass;
+    pass = pass_to_run(a.st);
+    if (pass < 0) return;
   } else {
     pass = a.eval_sel;
   }
@@ -765,9 +764,8 @@ __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) fista_pass_kernel(
 // (b = upd_block0 + blockIdx.x; parts = upd_parts, or the grid).
 template <int KP, bool MIXED>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) update_kernel(PassArgs a) {
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = pass_to_run(a.st);
+  if (pass < 0) return;
   const int parts = a.upd_parts > 0 ? a.upd_parts : (int)gridDim.x;
   const int b = a.upd_block0 + (int)blockIdx.x;
   const int64_t p0 = a.n * (int64_t)b / parts;
@@ -785,9 +783,8 @@ __global__ void __launch_bounds__(Lay<KP>::NT) heavy_kernel(PassArgs a) {
   using L = Lay<KP>;
   int64_t pass;
   if constexpr (!EVAL) {
-    volatile FistaState* vs = a.st;
-    if (vs->done || vs->pass >= vs->limit) return;
-    pass = vs->pass;
+    pass = pass_to_run(a.st);
+    if (pass < 0) return;
   } else {
     pass = a.eval_sel;
   }
@@ -852,11 +849,15 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   constexpr int E2 = KP * KP;
   FistaState* st = f.st;
   volatile FistaState* vs = st;
-  if (!f.eval && (vs->done || vs->pass >= vs->limit)) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = f.eval ? (int64_t)vs->pass : pass_to_run(st);
+  if (pass < 0) return;
   const int64_t nnew = pass + 1;
   const int tid = threadIdx.x;
   const int nent = f.eval ? E2 : 2 * E2;
+  // issued with the partials' loads rather than after them (only the last
+  // block writes shift, after every block has passed this point)
+  const int k = st->k;
+  const double shift = f.eval ? 0.0 : st->shift;
   {
     constexpr int EPB = fold_epb<KP>(), GR = 256 / EPB;
     __shared__ double gsum[256];
@@ -904,10 +905,9 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
         if (m == 0) {
           a2 = t * t;
         } else {
-          const int kk = st->k;
-          const bool in = r < kk && c < kk;
+          const bool in = r < k && c < k;
           gs = in ? t : 0.0;
-          f.Gy[r * KP + c] = in ? (float)(t - st->shift) : 0.0f;
+          f.Gy[r * KP + c] = in ? (float)(t - shift) : 0.0f;
         }
       }
     }
@@ -942,7 +942,6 @@ __device__ __forceinline__ void fold_body(const FoldArgs& f, int blk, int nblock
   if (!is_last) return;
   __threadfence();
 
-  const int k = st->k;
   const int warp = tid >> 5, lane = tid & 31;
   // Six sums, each thread's share in index order (t, t + 256, ...), then a
   // fixed butterfly across the lanes and the warps in warp order

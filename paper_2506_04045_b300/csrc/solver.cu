@@ -774,7 +774,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   c->split = opt.fused_pass == 0;
   // tcgen05 per-block update: engine 2 (and 3 where the streaming form does
   // not apply) for k in 17..64.  Engine 0 takes the warp form wherever it does
-  // not stream: its 16-row tiles keep more rows in flight per SM than the
+  // not stream: its resident blocks keep more rows in flight per SM than the
   // per-block tcgen05 kernel's chain of short MMA round trips (per iteration,
   // k = 32: 47.1 vs 52.1 us at n = 20,000, 66.0 vs 78.4 us at n = 60,000;
   // k = 64 class of the batched workload: 2.9 vs 3.2 ms; the k = 32 class:

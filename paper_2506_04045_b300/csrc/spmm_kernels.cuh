@@ -87,9 +87,8 @@ __host__ __device__ constexpr int spmm_min_blocks() {
 // of dependent loads sets the launch's time).
 template <int KP, bool MIXED, int RPU = kRowsPerUnit>
 __global__ void __launch_bounds__(Lay<KP>::NT, spmm_min_blocks<KP, MIXED>()) spmm_kernel(PassArgs a) {
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = pass_to_run(a.st);
+  if (pass < 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t units = a.unit_hi < 0 ? spmm_units<KP, MIXED, RPU>(a.n, a.n_heavy, a.n_chunks) : a.unit_hi;
   for (;;) {
@@ -125,9 +124,8 @@ __device__ __forceinline__ void finalize_row(const PassArgs& a, int64_t pass, in
 template <int KP>
 __global__ void __launch_bounds__(256) heavy_finalize_kernel(PassArgs a) {
   using L = Lay<KP>;
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = pass_to_run(a.st);
+  if (pass < 0) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t teams = (int64_t)gridDim.x * blockDim.x / L::T;
   for (int64_t p = t / L::T; p < a.n_heavy; p += teams) finalize_row<KP>(a, pass, p, (int)(t % L::T));

@@ -670,8 +670,8 @@ template <bool MIXED, bool FULL>
 __global__ void __launch_bounds__(ts::NT, 1) update_stream_kernel(PassArgs a, const __grid_constant__ StreamMaps maps) {
   using namespace ts;
   volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = pass_to_run(a.st);
+  if (pass < 0) return;
   extern __shared__ __align__(1024) uint8_t ts_smem_raw[];
   __shared__ __align__(8) uint64_t bars[NBARS];
   __shared__ uint32_t tslot;

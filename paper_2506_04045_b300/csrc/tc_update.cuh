@@ -549,9 +549,8 @@ __device__ __forceinline__ void tc_update_range(const PassArgs& a, int64_t pass,
 // rows [b n / parts, (b+1) n / parts) and partial slot b (as update_kernel).
 template <int KP, bool MIXED>
 __global__ void __launch_bounds__(Lay<KP>::NT, Lay<KP>::MINB) update_tc_kernel(PassArgs a) {
-  volatile FistaState* vs = a.st;
-  if (vs->done || vs->pass >= vs->limit) return;
-  const int64_t pass = vs->pass;
+  const int64_t pass = pass_to_run(a.st);
+  if (pass < 0) return;
   const int parts = a.upd_parts > 0 ? a.upd_parts : (int)gridDim.x;
   const int blk = a.upd_block0 + (int)blockIdx.x;
   const int64_t p0 = a.n * (int64_t)blk / parts;
