@@ -400,13 +400,6 @@ static void l2_setaside_release() {
 static const int64_t kMinTilesPerBlock = 32;
 // overlapped pass: minimum rows, and update blocks per resident update block
 static const int64_t kOvlMinRows = 1 << 20;
-// Floor of the chunk threshold H (nonzeros) of the split gather: a row of up to
-// H nonzeros is gathered by one team in H / 8 dependent batches, which sets the
-// launch's critical path in a small problem (n = 2037, k = 8: 31.6 us per
-// iteration with 64, 28.9 with 32, 28.1 with 16; 16 slowed k = 32..128 solves
-// of 6k..20k rows by 4-14% through the extra chunk sums, 32 none of those
-// measured up to n = 200k).
-static const int64_t kHeavyMin = 32;
 // update_engine 0 takes the streaming update for solvers of at least this many
 // articles (a persistent grid of one CTA per SM needs a few tiles per CTA)
 static const int64_t kStreamMinRows = 1 << 17;
@@ -816,7 +809,7 @@ cluster_status init_impl(const cluster_csr* S, int32_t k, const float* U0, const
   // of a unit in turn) sets the critical path of the launch
   {
     const int64_t warps = (int64_t)(c->split ? c->spmm_grid : c->heavy_grid) * 8;
-    c->heavy_H = std::max<int64_t>(kHeavyMin, std::min<int64_t>(16384 / c->KP, nnz / std::max<int64_t>(1, 8 * warps)));
+    c->heavy_H = std::max<int64_t>(64, std::min<int64_t>(16384 / c->KP, nnz / std::max<int64_t>(1, 8 * warps)));
   }
   c->row_cost = 6;
   FC_TRY(build_schedule(c));
