@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--budget-gb", type=float, default=120.0)
     p.add_argument("--serve-max-iter", type=int, default=5000)
     p.add_argument("--serve-tol", type=float, default=1e-5)
-    p.add_argument("--tick", type=int, default=16)
+    p.add_argument("--tick", type=int, default=64)
     p.add_argument("--instances", type=int, default=512)
     p.add_argument("--extras", default="batch,serve",
                    help="paper workload: also measure these forms in the same run (single GPU): batch "

@@ -388,7 +388,7 @@ typedef struct cluster_server_options {
                               tol 1e-5, max_iter 5000                          */
   size_t hbm_budget;       /* device bytes resident solves may use; 0 = 80% of
                               the free device memory at create time            */
-  int32_t iters_per_tick;  /* default 16                                        */
+  int32_t iters_per_tick;  /* default 64                                        */
   int32_t max_resident;    /* 0 = no limit besides the budget                   */
   int32_t borrow_host;     /* 1 = submit keeps pointers to the caller's host
                               arrays instead of copying them; they must stay

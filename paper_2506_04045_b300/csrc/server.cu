@@ -361,7 +361,7 @@ extern "C" void cluster_server_options_default(cluster_server_options* o) {
   o->solve.tol = 1e-5;
   o->solve.max_iter = 5000;
   o->hbm_budget = 0;
-  o->iters_per_tick = 16;
+  o->iters_per_tick = 64;
   o->max_resident = 0;
 }
 
